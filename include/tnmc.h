@@ -1,0 +1,198 @@
+/*
+ * tnmc.h - C ABI of the batched Tensor Network Monte Carlo hot path
+ * (arXiv 2509.19006, "BatchTNMC") for one NVIDIA B300 (sm_103a).
+ *
+ * The library runs, for a batch of 2D Edwards-Anderson disorder
+ * realizations of possibly different sizes L_n (open boundaries):
+ *   (a) the bottom-up boundary-MPS environments (Sec. 2.2, Sec. 3.2, Fig. 2):
+ *       each row's transfer MPO applied to the bond-chi MPS and truncated
+ *       back to chi by QR / SVD;
+ *   (b) row-by-row, spin-by-spin ancestral proposals with their log q
+ *       (Sec. 2.3 Eq. 9, Sec. 3.3);
+ *   (c) the exact energy (Eq. 1) and the independence Metropolis-Hastings
+ *       accept of Eq. 10;
+ * and log Z from the top-row environment (Eq. 6).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Memory: the caller owns every buffer. The library allocates no device
+ *   memory: everything it needs lives in one caller-provided workspace
+ *   (size from tnmc_workspace_size). The handle itself is a small host
+ *   struct created by tnmc_create and released by tnmc_destroy.
+ * - Streams: every call enqueues its kernels on the stream given to
+ *   tnmc_create and returns without waiting (except tnmc_create and
+ *   tnmc_get_device_status, which synchronise that stream).
+ * - Pointers named d_* are device pointers, h_* host pointers.
+ * - Errors: argument, state and launch errors are returned synchronously.
+ *   Errors found by the kernels (bad couplings, a numerical breakdown, a
+ *   bounded wait that ran out) are recorded per realization in device
+ *   flags read by tnmc_get_device_status. No call aborts, traps or prints.
+ * - Spin bits: 1 means s = +1, 0 means s = -1 (Sec. 3.3 uses 2*cfg-1).
+ *   Sites of a realization are stored in raster order i = r*L + c, r = 0
+ *   the top row (Eq. 3, Fig. 1a).
+ * - Batched arrays: realization n's block starts after the blocks of
+ *   realizations 0..n-1 (L_m^2 sites each, times S samples where the array
+ *   holds S configurations per realization).
+ * - Random numbers: Philox4x64-10 (Salmon et al., SC'11), key (seed, 0);
+ *   spin draw of site i of proposal id t in realization n uses counter
+ *   (i >> 2, t, n, 0) word i & 3; the accept test of proposal t uses
+ *   (0, t, n, 1) word 0; the random initial state uses (i >> 2, 0, n, 2)
+ *   word i & 3. A word w becomes u = (2 (w >> 12) + 1) 2^-53.
+ */
+#ifndef TNMC_H
+#define TNMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TNMC_OK = 0,
+  TNMC_ERR_ARG = 1,          /* a bad argument (null pointer, size out of range) */
+  TNMC_ERR_WORKSPACE = 2,    /* workspace too small or misaligned */
+  TNMC_ERR_CUDA = 3,         /* a CUDA runtime call or a kernel launch failed */
+  TNMC_ERR_NUMERIC = 4,      /* device flag: NaN/Inf or a vanishing norm */
+  TNMC_ERR_TIMEOUT = 5,      /* device flag: a bounded wait ran out */
+  TNMC_ERR_STATE = 6,        /* calls out of order (e.g. propose before build) */
+  TNMC_ERR_UNSUPPORTED = 7   /* a valid request this build does not implement */
+} tnmc_status;
+
+/* Arithmetic of the environment build and of the sampling contractions.
+ * Log scales, log q, log p and energies are float64 in every mode. */
+typedef enum {
+  TNMC_FP64 = 0,   /* all tensor arithmetic and the cache in float64 */
+  TNMC_FP32 = 1,   /* all tensor arithmetic and the cache in float32 */
+  TNMC_TF32 = 2,   /* reserved: tensor-core TF32 contractions */
+  TNMC_BF16 = 3    /* reserved: tensor-core BF16 contractions */
+} tnmc_prec;
+
+/* Device flags (bit mask per realization) reported by tnmc_get_device_status. */
+#define TNMC_FLAG_BAD_COUPLINGS 1  /* layout inconsistent, border not zero, or not finite */
+#define TNMC_FLAG_NUMERIC 2        /* NaN/Inf, or both conditionals of a draw vanished */
+#define TNMC_FLAG_TIMEOUT 4        /* a bounded device wait gave up */
+
+typedef struct {
+  int32_t n_real;        /* number of disorder realizations, >= 1 */
+  const int32_t *L;      /* host array [n_real]: side L_n of each realization, 1 <= L_n <= 4096 */
+  int32_t chi;           /* maximum bond dimension of the boundary MPS, 1 <= chi <= 64 */
+  double beta;           /* inverse temperature, finite, >= 0 */
+  int32_t prec;          /* tnmc_prec */
+  int32_t max_samples;   /* largest S passed to propose / score / mh_step, >= 1 */
+  double cutoff;         /* relative singular-value cutoff of the truncation (Sec. 1's
+                            truncation threshold): at each bond keep the chi largest
+                            singular values that exceed cutoff * (largest). <= 0 selects
+                            the default of the precision: 1e-12 (FP64), 1e-6 (FP32).
+                            Numerically-zero singular values must be dropped: their
+                            noise directions grow under the next rows' transfer MPOs. */
+} tnmc_config;
+
+typedef struct tnmc_handle tnmc_handle;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *tnmc_status_string(tnmc_status s);
+
+/* Bytes of device workspace a configuration needs (written to *bytes).
+ * The size covers the coupling copy, the environment cache (L_n^2 sites of
+ * chi x chi values per realization), the per-row log scales and bond sector
+ * sizes, and the scratch of the environment build and of the sampler
+ * (right environments of max_samples chains). Errors: TNMC_ERR_ARG. */
+tnmc_status tnmc_workspace_size(const tnmc_config *cfg, size_t *bytes);
+
+/* Bind a configuration to a workspace and a CUDA stream.
+ * d_ws: device pointer, 256-byte aligned, at least tnmc_workspace_size bytes;
+ *       owned by the caller and used by the handle until tnmc_destroy.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Copies the per-realization table to the workspace and synchronises the
+ * stream once. Errors: TNMC_ERR_ARG, TNMC_ERR_WORKSPACE, TNMC_ERR_CUDA. */
+tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes,
+                        void *cuda_stream, tnmc_handle **out);
+
+/* Release the host handle (the workspace stays the caller's). NULL is a no-op. */
+void tnmc_destroy(tnmc_handle *h);
+
+/* Build the boundary-MPS environments of every realization (Sec. 3.2 and
+ * Sec. 3.4: the bottom-row MPS, then for rows L-2..0 the row MPO applied to
+ * the MPS below and compressed to chi by a left-to-right QR sweep and a
+ * right-to-left truncating SVD sweep).
+ * d_J: couplings in the paper's layout (Sec. 3.1): for each realization an
+ *      (L_n, L_n, 4) float32 block, (left, up, right, down) per site, 0 on
+ *      the open boundary; blocks concatenated over n ((sum L_n^2) x 4 floats).
+ *      Read during this call's kernels only; the library keeps its own copy.
+ * Realizations whose couplings fail the checks get TNMC_FLAG_BAD_COUPLINGS.
+ * Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+tnmc_status tnmc_build_envs(tnmc_handle *h, const float *d_J);
+
+/* log Z of every realization from the top-row environment (Eq. 6):
+ * lambda_0 + log of the row-0 MPS with every physical leg summed.
+ * d_logz: float64 [n_real]. Errors: TNMC_ERR_ARG, TNMC_ERR_STATE, TNMC_ERR_CUDA. */
+tnmc_status tnmc_log_z(tnmc_handle *h, double *d_logz);
+
+/* Draw S proposals per realization (Sec. 3.3, Eq. 5 and Eq. 9), proposal ids
+ * prop_base .. prop_base + S - 1 (the Philox counters; distinct ids give
+ * independent proposals, equal ids reproduce them bit for bit).
+ * d_spins: uint8 [sum_n S L_n^2], raster order per configuration;
+ * d_logq : float64 [n_real * S], log q(s) of each proposal (the log of the
+ *          probabilities the draws were taken from);
+ * d_E    : float64 [n_real * S], the energy of Eq. 1 (exact for +-J).
+ * Errors: TNMC_ERR_ARG (S > max_samples), TNMC_ERR_STATE, TNMC_ERR_CUDA. */
+tnmc_status tnmc_propose(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop_base,
+                         uint8_t *d_spins, double *d_logq, double *d_E);
+
+/* Teacher-forced scoring: log q and E of S given configurations per
+ * realization (same layouts as tnmc_propose; d_spins is read-only here). */
+tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
+                       double *d_logq, double *d_E);
+
+/* Random initial chain state of every realization (uniform spins, Philox
+ * stream 2, proposal id 0) scored by the proposal q.
+ * d_state_spins: uint8 [sum L_n^2]; d_state_logq, d_state_E: float64 [n_real]. */
+tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
+                         double *d_state_logq, double *d_state_E);
+
+/* Independence Metropolis-Hastings (Eq. 10) over S proposals per
+ * realization, consumed in id order prop_base .. prop_base + S - 1: proposal
+ * t is accepted iff log u_t < (-beta E' - log q') - (-beta E - log q).
+ * d_prop_*  : the outputs of tnmc_propose for the same S and prop_base;
+ * d_state_* : the chain state, read and updated in place;
+ * d_accept  : uint8 [n_real * S], 1 where the proposal was accepted;
+ * d_n_accept: int64 [n_real], accepted proposals of this call added in.
+ * Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+tnmc_status tnmc_mh_step(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop_base,
+                         const uint8_t *d_prop_spins, const double *d_prop_logq,
+                         const double *d_prop_E, uint8_t *d_state_spins,
+                         double *d_state_logq, double *d_state_E, uint8_t *d_accept,
+                         int64_t *d_n_accept);
+
+/* Optional diagnostic outputs, written by later calls until reset with NULL.
+ * d_logits : float32 [n_real * S * L^2] of propose / score: the logit of Eq. 5
+ *            each draw was taken from (requires equal L for all realizations
+ *            or is indexed like d_spins);
+ * d_spectra: float64 [sum_n L_n (L_n + 1) chi] of build_envs: at row r,
+ *            bond b (between sites b-1 and b), the kept singular values
+ *            divided by the largest, in decreasing order, zero padded;
+ * d_rowinfo: float64 [sum_n L_n * 6] of build_envs: per row (log of the
+ *            2-norm of F_r, smallest relative gap s_kept/s_dropped - 1 at a
+ *            cut, largest discarded weight, bonds where values were dropped,
+ *            largest bond dimension, mean bond dimension). */
+tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spectra,
+                                 double *d_rowinfo);
+
+/* Copy the per-realization device flags (TNMC_FLAG_*) to h_flags [n_real],
+ * after synchronising the stream; clears them when clear != 0.
+ * Returns TNMC_OK, or TNMC_ERR_NUMERIC / TNMC_ERR_TIMEOUT if any flag of
+ * that kind is set (bad couplings map to TNMC_ERR_ARG). */
+tnmc_status tnmc_get_device_status(tnmc_handle *h, int32_t *h_flags, int32_t clear);
+
+/* Sizes of the internal layout, for tests: bytes of the cache, of the
+ * environment-build scratch and of the sampler scratch. */
+tnmc_status tnmc_layout_info(const tnmc_config *cfg, size_t *cache_bytes,
+                             size_t *env_scratch_bytes, size_t *sample_scratch_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNMC_H */

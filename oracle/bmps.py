@@ -19,8 +19,13 @@ Site tensors are float64 arrays (D_left, 2, D_right), index order
 
 Readings of points the paper leaves open (all listed in the design doc):
 * compress = a left-to-right QR sweep (left-canonical form), then a
-  right-to-left SVD sweep keeping the k = min(chi, available) largest singular
-  values at each bond; hard cut, no threshold.
+  right-to-left SVD sweep keeping, at each bond, the singular values that are
+  among the chi largest AND above cutoff * (largest) -- the "truncation
+  threshold" of Sec. 1. The threshold is not optional in practice: keeping
+  numerically-zero singular values lets their noise directions grow under the
+  next rows' transfer MPOs (at beta = 3, L = 32, log Z then drifts by ~10 as
+  chi grows while the discarded weight is 1e-19); the default 1e-12 is far
+  above float64 rounding and far below any physical weight.
 * Boltzmann matrices are used normalised (entries {1, exp(-2 beta |J|)}), the
   removed factor exp(beta |J|) and every renormalisation go into a float64 log
   scale lambda_r, so F_r = exp(lambda_r) * contraction(tensors).
@@ -112,12 +117,16 @@ def multiply(mpo: List[np.ndarray], mps: List[np.ndarray]) -> List[np.ndarray]:
     return out
 
 
-def compress(mps: List[np.ndarray], chi: int):
+DEFAULT_CUTOFF = 1e-12
+
+
+def compress(mps: List[np.ndarray], chi: int, cutoff: float = DEFAULT_CUTOFF):
     """Bring every bond to at most chi (Sec. 2.2, Sec. 3.2 ``compress``).
 
     1. Left-to-right QR sweep: A_c = Q R, A_c <- Q, A_{c+1} <- R A_{c+1}.
     2. Right-to-left SVD sweep: A_c (as D_l x (2 D_r)) = U S V^T, keep the k
-       largest singular values, A_c <- V^T[:k], A_{c-1} <- A_{c-1} U[:, :k] S[:k].
+       largest singular values (k <= chi, S[k-1] > cutoff * S[0], k >= 1),
+       A_c <- V^T[:k], A_{c-1} <- A_{c-1} U[:, :k] S[:k].
     3. Site 0 is divided by its Frobenius norm.
     Every division by a norm is added to the returned log scale. Returns
     (tensors, log_scale, spectra, cut_gap, discarded); the diagnostics are
@@ -139,7 +148,7 @@ def compress(mps: List[np.ndarray], chi: int):
     for c in range(L - 1, 0, -1):
         Dl, _, Dr = mps[c].shape
         U, S, Vh = np.linalg.svd(mps[c].reshape(Dl, 2 * Dr), full_matrices=False)
-        k = min(chi, S.size)
+        k = min(chi, S.size, max(1, int(np.sum(S > cutoff * S[0]))))
         total = float(np.sum(S ** 2))
         if k < S.size:
             gaps[c] = (S[k - 1] / S[k] - 1.0) if S[k] > 0 else np.inf
@@ -155,7 +164,8 @@ def compress(mps: List[np.ndarray], chi: int):
     return mps, log_scale, spectra[1:], gaps[1:], disc[1:]
 
 
-def build_envs(Jh: np.ndarray, Jv: np.ndarray, beta: float, chi: int) -> List[RowEnv]:
+def build_envs(Jh: np.ndarray, Jv: np.ndarray, beta: float, chi: int,
+               cutoff: float = DEFAULT_CUTOFF) -> List[RowEnv]:
     """Sec. 3.2 ``create_cache_ising``: the cache rows L-1 .. 0, returned indexed by row.
 
     Row L-1 is the bottom-row MPS (compressed like every other row so that all
@@ -172,7 +182,7 @@ def build_envs(Jh: np.ndarray, Jv: np.ndarray, beta: float, chi: int) -> List[Ro
             mps = multiply(mpo, mps)
             lam += sc
         if L > 1:
-            mps, sc, spec, gaps, disc = compress(mps, chi)
+            mps, sc, spec, gaps, disc = compress(mps, chi, cutoff)
         else:
             spec, gaps, disc, sc = [], [], [], 0.0
         lam += sc

@@ -1,0 +1,265 @@
+"""Python binding of ``libtnmc.so``, the batched TNMC hot path on one B300.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. torch supplies device memory (the workspace and the caller's
+buffers) and the CUDA stream. There is no CPU fallback: if the library is
+missing or no CUDA device is present the calls raise.
+
+The names follow the C ABI in ``include/tnmc.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtnmc.so")
+
+TNMC_FP64, TNMC_FP32, TNMC_TF32, TNMC_BF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": TNMC_FP64, "fp32": TNMC_FP32, "tf32": TNMC_TF32, "bf16": TNMC_BF16}
+FLAG_BAD_COUPLINGS, FLAG_NUMERIC, FLAG_TIMEOUT = 1, 2, 4
+
+EXPORTED = [
+    "tnmc_status_string", "tnmc_workspace_size", "tnmc_create", "tnmc_destroy",
+    "tnmc_build_envs", "tnmc_log_z", "tnmc_propose", "tnmc_score", "tnmc_mh_init",
+    "tnmc_mh_step", "tnmc_set_diagnostics", "tnmc_get_device_status", "tnmc_layout_info",
+]
+
+
+class TnmcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("n_real", ctypes.c_int32),
+        ("L", ctypes.POINTER(ctypes.c_int32)),
+        ("chi", ctypes.c_int32),
+        ("beta", ctypes.c_double),
+        ("prec", ctypes.c_int32),
+        ("max_samples", ctypes.c_int32),
+        ("cutoff", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libtnmc.so (raises ImportError when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libtnmc.so not built (expected at {LIB_PATH}); run the package build")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u64, i32, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32, ctypes.c_size_t
+    cfgp = ctypes.POINTER(_Config)
+    sig = {
+        "tnmc_status_string": ([i32], ctypes.c_char_p),
+        "tnmc_workspace_size": ([cfgp, ctypes.POINTER(sz)], i32),
+        "tnmc_layout_info": ([cfgp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(sz)], i32),
+        "tnmc_create": ([cfgp, vp, sz, vp, ctypes.POINTER(vp)], i32),
+        "tnmc_destroy": ([vp], None),
+        "tnmc_build_envs": ([vp, vp], i32),
+        "tnmc_log_z": ([vp, vp], i32),
+        "tnmc_propose": ([vp, i32, u64, u64, vp, vp, vp], i32),
+        "tnmc_score": ([vp, i32, vp, vp, vp], i32),
+        "tnmc_mh_init": ([vp, u64, vp, vp, vp], i32),
+        "tnmc_mh_step": ([vp, i32, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp], i32),
+        "tnmc_set_diagnostics": ([vp, vp, vp, vp], i32),
+        "tnmc_get_device_status": ([vp, vp, i32], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load_library().tnmc_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise TnmcError(status, what)
+
+
+def _cfg(Ls: Sequence[int], chi: int, beta: float, prec: int, max_samples: int, cutoff: float = 0.0):
+    arr = (ctypes.c_int32 * len(Ls))(*[int(x) for x in Ls])
+    cfg = _Config(len(Ls), ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)), int(chi),
+                  float(beta), int(prec), int(max_samples), float(cutoff))
+    return cfg, arr
+
+
+def workspace_size(Ls, chi, beta, prec, max_samples, cutoff=0.0) -> int:
+    lib = load_library()
+    cfg, keep = _cfg(Ls, chi, beta, prec, max_samples, cutoff)
+    out = ctypes.c_size_t(0)
+    _check(lib.tnmc_workspace_size(ctypes.byref(cfg), ctypes.byref(out)), "tnmc_workspace_size")
+    return out.value
+
+
+def layout_info(Ls, chi, beta, prec, max_samples):
+    lib = load_library()
+    cfg, keep = _cfg(Ls, chi, beta, prec, max_samples)
+    a, b, c = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(lib.tnmc_layout_info(ctypes.byref(cfg), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "tnmc_layout_info")
+    return a.value, b.value, c.value
+
+
+def _ptr(t) -> int:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class Proposals:
+    spins: "object"   # torch.uint8 [sum_n S L_n^2]
+    logq: "object"    # torch.float64 [n_real, S]
+    E: "object"       # torch.float64 [n_real, S]
+    S: int
+    prop_base: int
+
+
+@dataclass
+class ChainState:
+    spins: "object"   # torch.uint8 [sum_n L_n^2]
+    logq: "object"    # torch.float64 [n_real]
+    E: "object"       # torch.float64 [n_real]
+    n_accept: "object"  # torch.int64 [n_real]
+
+
+class TNMC:
+    """A handle on the library for one batch of realizations on one CUDA device."""
+
+    DEFAULT_CUTOFF = {TNMC_FP64: 1e-12, TNMC_FP32: 1e-6}
+
+    def __init__(self, Ls: Sequence[int], chi: int, beta: float, prec: str | int = "fp32",
+                 max_samples: int = 256, device="cuda:0", stream=None, cutoff: float = 0.0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("TNMC needs a CUDA device; there is no CPU fallback")
+        self.lib = load_library()
+        self.torch = torch
+        self.Ls = [int(x) for x in Ls]
+        self.chi, self.beta = int(chi), float(beta)
+        self.prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        self.max_samples = int(max_samples)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.n_real = len(self.Ls)
+        self.sum_L2 = sum(L * L for L in self.Ls)
+        self.cutoff = float(cutoff) if cutoff > 0 else self.DEFAULT_CUTOFF.get(self.prec, 1e-6)
+        self._cfg, self._cfg_keep = _cfg(self.Ls, chi, beta, self.prec, max_samples, self.cutoff)
+        nbytes = ctypes.c_size_t(0)
+        _check(self.lib.tnmc_workspace_size(ctypes.byref(self._cfg), ctypes.byref(nbytes)),
+               "tnmc_workspace_size")
+        self.ws_bytes = nbytes.value
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        h = ctypes.c_void_p(0)
+        _check(self.lib.tnmc_create(ctypes.byref(self._cfg), ctypes.c_void_p(self._ws_ptr),
+                                    self.ws_bytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                    ctypes.byref(h)), "tnmc_create")
+        self.h = h
+        self._diag = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tnmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ calls
+    def build_envs(self, J):
+        """J: float32 device tensor (sum L^2, 4) in the paper's (left, up, right, down) layout."""
+        assert J.dtype == self.torch.float32 and J.is_cuda and J.is_contiguous()
+        assert J.numel() == 4 * self.sum_L2
+        self._J_keep = J
+        _check(self.lib.tnmc_build_envs(self.h, _ptr(J)), "tnmc_build_envs")
+
+    def log_z(self, out=None):
+        out = out if out is not None else self.torch.empty(self.n_real, dtype=self.torch.float64, device=self.device)
+        _check(self.lib.tnmc_log_z(self.h, _ptr(out)), "tnmc_log_z")
+        return out
+
+    def alloc_proposals(self, S: int, prop_base: int = 0) -> Proposals:
+        t = self.torch
+        return Proposals(t.empty(S * self.sum_L2, dtype=t.uint8, device=self.device),
+                         t.empty((self.n_real, S), dtype=t.float64, device=self.device),
+                         t.empty((self.n_real, S), dtype=t.float64, device=self.device), S, prop_base)
+
+    def propose(self, S: int, seed: int, prop_base: int = 0, out: Optional[Proposals] = None) -> Proposals:
+        out = out if out is not None else self.alloc_proposals(S, prop_base)
+        out.S, out.prop_base = S, prop_base
+        _check(self.lib.tnmc_propose(self.h, int(S), int(seed), int(prop_base), _ptr(out.spins),
+                                     _ptr(out.logq), _ptr(out.E)), "tnmc_propose")
+        return out
+
+    def score(self, spins, S: int):
+        t = self.torch
+        lq = t.empty((self.n_real, S), dtype=t.float64, device=self.device)
+        E = t.empty((self.n_real, S), dtype=t.float64, device=self.device)
+        _check(self.lib.tnmc_score(self.h, int(S), _ptr(spins), _ptr(lq), _ptr(E)), "tnmc_score")
+        return lq, E
+
+    def mh_init(self, seed: int) -> ChainState:
+        t = self.torch
+        st = ChainState(t.empty(self.sum_L2, dtype=t.uint8, device=self.device),
+                        t.empty(self.n_real, dtype=t.float64, device=self.device),
+                        t.empty(self.n_real, dtype=t.float64, device=self.device),
+                        t.zeros(self.n_real, dtype=t.int64, device=self.device))
+        _check(self.lib.tnmc_mh_init(self.h, int(seed), _ptr(st.spins), _ptr(st.logq), _ptr(st.E)),
+               "tnmc_mh_init")
+        return st
+
+    def mh_step(self, props: Proposals, state: ChainState, seed: int, accept=None):
+        t = self.torch
+        acc = accept if accept is not None else t.empty((self.n_real, props.S), dtype=t.uint8, device=self.device)
+        _check(self.lib.tnmc_mh_step(self.h, int(props.S), int(seed), int(props.prop_base),
+                                     _ptr(props.spins), _ptr(props.logq), _ptr(props.E),
+                                     _ptr(state.spins), _ptr(state.logq), _ptr(state.E), _ptr(acc),
+                                     _ptr(state.n_accept)), "tnmc_mh_step")
+        return acc
+
+    def set_diagnostics(self, S: int = 0, logits: bool = False, spectra: bool = False, rowinfo: bool = False):
+        """Allocate and register the optional diagnostic outputs (None disables)."""
+        t = self.torch
+        lg = t.zeros(S * self.sum_L2, dtype=t.float32, device=self.device) if logits else None
+        sp = t.zeros(sum(L * (L + 1) for L in self.Ls) * self.chi, dtype=t.float64, device=self.device) if spectra else None
+        ri = t.zeros(sum(self.Ls) * 6, dtype=t.float64, device=self.device) if rowinfo else None
+        self._diag = (lg, sp, ri)
+        z = ctypes.c_void_p(0)
+        _check(self.lib.tnmc_set_diagnostics(self.h, _ptr(lg) if lg is not None else z,
+                                             _ptr(sp) if sp is not None else z,
+                                             _ptr(ri) if ri is not None else z), "tnmc_set_diagnostics")
+        return self._diag
+
+    def device_status(self, clear: bool = True):
+        """(status code, per-realization flags) after synchronising the stream."""
+        import numpy as np
+        flags = np.zeros(self.n_real, dtype=np.int32)
+        st = self.lib.tnmc_get_device_status(self.h, flags.ctypes.data_as(ctypes.c_void_p), int(bool(clear)))
+        return st, flags
+
+    # ------------------------------------------------------------------ helpers
+    def spin_offsets(self, S: int) -> List[int]:
+        """Start of each realization's block in a spins array holding S configurations each."""
+        offs, o = [], 0
+        for L in self.Ls:
+            offs.append(o)
+            o += S * L * L
+        return offs

@@ -1,0 +1,317 @@
+// C ABI of the TNMC library (include/tnmc.h): workspace planning, argument
+// checks and kernel launches. No device memory is allocated here.
+#include "../../include/tnmc.h"
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <numeric>
+#include <vector>
+
+namespace tnmc {
+cudaError_t launch_ingest(const Layout &lay, const float *J, cudaStream_t st);
+cudaError_t launch_env_build(const Layout &lay, int prec, int CH, cudaStream_t st);
+cudaError_t launch_log_z(const Layout &lay, int prec, double *logz, cudaStream_t st);
+cudaError_t launch_init_state(const Layout &lay, uint64_t seed, uint8_t *spins, cudaStream_t st);
+cudaError_t launch_mh(const Layout &lay, int S, uint64_t seed, uint64_t base, const uint8_t *ps,
+                      const double *pl, const double *pe, uint8_t *ss, double *sl, double *se,
+                      uint8_t *acc, int64_t *nacc, cudaStream_t st);
+cudaError_t launch_propose(const Layout &lay, int prec, int CH, int S, uint64_t seed,
+                           uint64_t base, uint8_t *spins, double *lq, double *E, cudaStream_t st);
+cudaError_t launch_score(const Layout &lay, int prec, int CH, int S, const uint8_t *spins,
+                         double *lq, double *E, cudaStream_t st);
+int64_t env_slot_bytes(int prec, int CH, int L_max);
+int64_t sampler_smem_bytes(int prec, int CH, int L_max);
+}  // namespace tnmc
+
+using namespace tnmc;
+
+namespace {
+
+constexpr int kMaxL = 4096;
+constexpr int kEnvSlots = 148;   // concurrent realizations of the environment build (SM count)
+
+struct Plan {
+  int CH = 0;
+  int64_t sum_L2 = 0, sum_L = 0, sum_bonds = 0;
+  int L_max = 0;
+  int64_t off_reals, off_order, off_flags, off_counter, off_jr, off_jd, off_cache, off_bonds,
+      off_lam, off_env, off_samp, total;
+  int64_t cache_bytes, env_bytes, samp_bytes, env_slot;
+  int env_slots;
+};
+
+int pick_ch(int chi) {
+  for (int ch : {8, 16, 32, 64})
+    if (chi <= ch) return ch;
+  return -1;
+}
+
+tnmc_status check_cfg(const tnmc_config *cfg) {
+  if (!cfg || !cfg->L || cfg->n_real < 1) return TNMC_ERR_ARG;
+  if (cfg->chi < 1 || cfg->chi > 64) return TNMC_ERR_ARG;
+  if (!std::isfinite(cfg->beta) || cfg->beta < 0) return TNMC_ERR_ARG;
+  if (cfg->max_samples < 1 || cfg->max_samples > (1 << 24)) return TNMC_ERR_ARG;
+  if (!std::isfinite(cfg->cutoff) || cfg->cutoff >= 1.0) return TNMC_ERR_ARG;
+  if (cfg->prec == TNMC_TF32 || cfg->prec == TNMC_BF16) return TNMC_ERR_UNSUPPORTED;
+  if (cfg->prec != TNMC_FP64 && cfg->prec != TNMC_FP32) return TNMC_ERR_ARG;
+  for (int n = 0; n < cfg->n_real; ++n)
+    if (cfg->L[n] < 1 || cfg->L[n] > kMaxL) return TNMC_ERR_ARG;
+  return TNMC_OK;
+}
+
+Plan make_plan(const tnmc_config *cfg) {
+  Plan p;
+  p.CH = pick_ch(cfg->chi);
+  const int64_t esz = cfg->prec == TNMC_FP64 ? 8 : 4;
+  for (int n = 0; n < cfg->n_real; ++n) {
+    const int64_t L = cfg->L[n];
+    p.sum_L2 += L * L;
+    p.sum_L += L;
+    p.sum_bonds += L * (L + 1);
+    p.L_max = std::max<int>(p.L_max, int(L));
+  }
+  int64_t o = 0;
+  auto take = [&](int64_t bytes) { const int64_t at = o; o += align256(bytes); return at; };
+  p.off_reals = take(int64_t(cfg->n_real) * sizeof(RealInfo));
+  p.off_order = take(int64_t(cfg->n_real) * 4);
+  p.off_flags = take(int64_t(cfg->n_real) * 4);
+  p.off_counter = take(64 * 4);
+  p.off_jr = take(p.sum_L2 * 4);
+  p.off_jd = take(p.sum_L2 * 4);
+  p.cache_bytes = p.sum_L2 * int64_t(cfg->chi) * cfg->chi * esz;
+  p.off_cache = take(p.cache_bytes);
+  p.off_bonds = take(p.sum_bonds * 8);
+  p.off_lam = take(p.sum_L * 8);
+  p.env_slots = std::min(cfg->n_real, kEnvSlots);
+  p.env_slot = env_slot_bytes(cfg->prec == TNMC_FP64 ? 0 : 1, p.CH, p.L_max);
+  p.env_bytes = p.env_slot * p.env_slots;
+  p.off_env = take(p.env_bytes);
+  p.samp_bytes = int64_t(cfg->max_samples) * p.sum_L * p.CH * esz;
+  p.off_samp = take(p.samp_bytes);
+  p.total = o;
+  return p;
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+struct tnmc_handle {
+  std::vector<int32_t> L;
+  tnmc_config cfg;
+  Plan plan;
+  Layout lay;
+  int prec_code;   // 0 = float64 kernels, 1 = float32 kernels
+  cudaStream_t stream;
+  bool built = false;
+};
+
+extern "C" {
+
+const char *tnmc_status_string(tnmc_status s) {
+  switch (s) {
+    case TNMC_OK: return "ok";
+    case TNMC_ERR_ARG: return "invalid argument";
+    case TNMC_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case TNMC_ERR_CUDA: return "CUDA error";
+    case TNMC_ERR_NUMERIC: return "numerical breakdown (device flag)";
+    case TNMC_ERR_TIMEOUT: return "bounded device wait ran out (device flag)";
+    case TNMC_ERR_STATE: return "call out of order";
+    case TNMC_ERR_UNSUPPORTED: return "not supported by this build";
+  }
+  return "unknown status";
+}
+
+tnmc_status tnmc_workspace_size(const tnmc_config *cfg, size_t *bytes) {
+  if (!bytes) return TNMC_ERR_ARG;
+  const tnmc_status s = check_cfg(cfg);
+  if (s != TNMC_OK) return s;
+  *bytes = size_t(make_plan(cfg).total);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_layout_info(const tnmc_config *cfg, size_t *cache_bytes, size_t *env_bytes,
+                             size_t *samp_bytes) {
+  const tnmc_status s = check_cfg(cfg);
+  if (s != TNMC_OK) return s;
+  const Plan p = make_plan(cfg);
+  if (cache_bytes) *cache_bytes = size_t(p.cache_bytes);
+  if (env_bytes) *env_bytes = size_t(p.env_bytes);
+  if (samp_bytes) *samp_bytes = size_t(p.samp_bytes);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, void *cuda_stream,
+                        tnmc_handle **out) {
+  if (!out) return TNMC_ERR_ARG;
+  *out = nullptr;
+  tnmc_status s = check_cfg(cfg);
+  if (s != TNMC_OK) return s;
+  const Plan p = make_plan(cfg);
+  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255) != 0 || ws_bytes < size_t(p.total))
+    return TNMC_ERR_WORKSPACE;
+  tnmc_handle *h = new (std::nothrow) tnmc_handle();
+  if (!h) return TNMC_ERR_ARG;
+  h->L.assign(cfg->L, cfg->L + cfg->n_real);
+  h->cfg = *cfg;
+  h->cfg.L = h->L.data();
+  h->plan = p;
+  h->prec_code = cfg->prec == TNMC_FP64 ? 0 : 1;
+  h->stream = as_stream(cuda_stream);
+  unsigned char *ws = static_cast<unsigned char *>(d_ws);
+
+  // per-realization table and the longest-first order
+  std::vector<RealInfo> reals(cfg->n_real);
+  int64_t so = 0, bo = 0, ro = 0;
+  for (int n = 0; n < cfg->n_real; ++n) {
+    const int64_t L = cfg->L[n];
+    reals[n].L = int32_t(L);
+    reals[n].pad = 0;
+    reals[n].site_off = so;
+    reals[n].bond_off = bo;
+    reals[n].row_off = ro;
+    reals[n].line_off = ro;
+    so += L * L; bo += L * (L + 1); ro += L;
+  }
+  std::vector<int32_t> order(cfg->n_real);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return cfg->L[a] > cfg->L[b]; });
+
+  Layout &lay = h->lay;
+  lay.reals = reinterpret_cast<const RealInfo *>(ws + p.off_reals);
+  lay.order = reinterpret_cast<const int32_t *>(ws + p.off_order);
+  lay.n_real = cfg->n_real;
+  lay.chi = cfg->chi;
+  lay.L_max = p.L_max;
+  lay.max_samples = cfg->max_samples;
+  lay.beta = cfg->beta;
+  lay.cutoff = cfg->cutoff > 0 ? cfg->cutoff : (cfg->prec == TNMC_FP64 ? 1e-12 : 1e-6);
+  lay.jr = reinterpret_cast<float *>(ws + p.off_jr);
+  lay.jd = reinterpret_cast<float *>(ws + p.off_jd);
+  lay.cache = ws + p.off_cache;
+  lay.bonds = reinterpret_cast<int2 *>(ws + p.off_bonds);
+  lay.lam = reinterpret_cast<double *>(ws + p.off_lam);
+  lay.flags = reinterpret_cast<int32_t *>(ws + p.off_flags);
+  lay.counter = reinterpret_cast<int32_t *>(ws + p.off_counter);
+  lay.env_scratch = ws + p.off_env;
+  lay.env_slot_bytes = p.env_slot;
+  lay.env_slots = p.env_slots;
+  lay.samp_scratch = ws + p.off_samp;
+  lay.dbg_logits = nullptr;
+  lay.dbg_spectra = nullptr;
+  lay.dbg_rowinfo = nullptr;
+
+  cudaError_t e = cudaMemcpyAsync(ws + p.off_reals, reals.data(), reals.size() * sizeof(RealInfo),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + p.off_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws + p.off_flags, 0, size_t(cfg->n_real) * 4, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return TNMC_ERR_CUDA;
+  }
+  *out = h;
+  return TNMC_OK;
+}
+
+void tnmc_destroy(tnmc_handle *h) { delete h; }
+
+tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spectra,
+                                 double *d_rowinfo) {
+  if (!h) return TNMC_ERR_ARG;
+  h->lay.dbg_logits = d_logits;
+  h->lay.dbg_spectra = d_spectra;
+  h->lay.dbg_rowinfo = d_rowinfo;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_build_envs(tnmc_handle *h, const float *d_J) {
+  if (!h || !d_J) return TNMC_ERR_ARG;
+  cudaError_t e = launch_ingest(h->lay, d_J, h->stream);
+  if (e == cudaSuccess && h->lay.dbg_spectra)
+    e = cudaMemsetAsync(h->lay.dbg_spectra, 0,
+                        size_t(h->plan.sum_bonds) * h->cfg.chi * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = launch_env_build(h->lay, h->prec_code, h->plan.CH, h->stream);
+  if (e != cudaSuccess) return TNMC_ERR_CUDA;
+  h->built = true;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_log_z(tnmc_handle *h, double *d_logz) {
+  if (!h || !d_logz) return TNMC_ERR_ARG;
+  if (!h->built) return TNMC_ERR_STATE;
+  return launch_log_z(h->lay, h->prec_code, d_logz, h->stream) == cudaSuccess ? TNMC_OK
+                                                                               : TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_propose(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop_base,
+                         uint8_t *d_spins, double *d_logq, double *d_E) {
+  if (!h || !d_spins || !d_logq || !d_E) return TNMC_ERR_ARG;
+  if (S < 1 || S > h->cfg.max_samples) return TNMC_ERR_ARG;
+  if (!h->built) return TNMC_ERR_STATE;
+  return launch_propose(h->lay, h->prec_code, h->plan.CH, S, seed, prop_base, d_spins, d_logq,
+                        d_E, h->stream) == cudaSuccess
+             ? TNMC_OK
+             : TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins, double *d_logq,
+                       double *d_E) {
+  if (!h || !d_spins || !d_logq || !d_E) return TNMC_ERR_ARG;
+  if (S < 1 || S > h->cfg.max_samples) return TNMC_ERR_ARG;
+  if (!h->built) return TNMC_ERR_STATE;
+  return launch_score(h->lay, h->prec_code, h->plan.CH, S, d_spins, d_logq, d_E, h->stream) ==
+                 cudaSuccess
+             ? TNMC_OK
+             : TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
+                         double *d_state_logq, double *d_state_E) {
+  if (!h || !d_state_spins || !d_state_logq || !d_state_E) return TNMC_ERR_ARG;
+  if (!h->built) return TNMC_ERR_STATE;
+  cudaError_t e = launch_init_state(h->lay, seed, d_state_spins, h->stream);
+  if (e == cudaSuccess)
+    e = launch_score(h->lay, h->prec_code, h->plan.CH, 1, d_state_spins, d_state_logq, d_state_E,
+                     h->stream);
+  return e == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_mh_step(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop_base,
+                         const uint8_t *d_prop_spins, const double *d_prop_logq,
+                         const double *d_prop_E, uint8_t *d_state_spins, double *d_state_logq,
+                         double *d_state_E, uint8_t *d_accept, int64_t *d_n_accept) {
+  if (!h || !d_prop_spins || !d_prop_logq || !d_prop_E || !d_state_spins || !d_state_logq ||
+      !d_state_E || !d_accept || !d_n_accept)
+    return TNMC_ERR_ARG;
+  if (S < 1 || S > h->cfg.max_samples) return TNMC_ERR_ARG;
+  return launch_mh(h->lay, S, seed, prop_base, d_prop_spins, d_prop_logq, d_prop_E, d_state_spins,
+                   d_state_logq, d_state_E, d_accept, d_n_accept, h->stream) == cudaSuccess
+             ? TNMC_OK
+             : TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_get_device_status(tnmc_handle *h, int32_t *h_flags, int32_t clear) {
+  if (!h || !h_flags) return TNMC_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(h_flags, h->lay.flags, size_t(h->cfg.n_real) * 4,
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && clear) {
+    e = cudaMemsetAsync(h->lay.flags, 0, size_t(h->cfg.n_real) * 4, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  if (e != cudaSuccess) return TNMC_ERR_CUDA;
+  int32_t any = 0;
+  for (int n = 0; n < h->cfg.n_real; ++n) any |= h_flags[n];
+  if (any & FLAG_NUMERIC) return TNMC_ERR_NUMERIC;
+  if (any & FLAG_TIMEOUT) return TNMC_ERR_TIMEOUT;
+  if (any & FLAG_BAD_J) return TNMC_ERR_ARG;
+  return TNMC_OK;
+}
+
+}  // extern "C"

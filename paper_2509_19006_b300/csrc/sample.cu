@@ -1,0 +1,417 @@
+// Row-by-row ancestral proposals and teacher-forced scoring (Sec. 3.3,
+// Eq. 4-5, Eq. 9), batched over realizations x samples (Sec. 3.4).
+//
+// A CTA owns 64 chains (samples) of one realization and walks the rows top to
+// bottom. For each row it runs
+//   right pass  c = L-2 .. 0 : R_c = T_{c+1}[s_up(c+1)] R_{c+1}, normalised,
+//                spilled to the sampler scratch;
+//   left pass   c = 0 .. L-1 : rho_s = | l M_c[s] R_c |, logit of Eq. 5, the
+//                Philox draw, log q (Eq. 9) and the energy (Eq. 1).
+// In parity form (common.cuh) M_c[s] = Pi^s C_c Pi^s, so with u = l_even C
+// and w = l_odd C (one chi x chi pass over C for both spin values):
+//   rho_0 = |(u + w) . R|,  rho_1 = |(u - w) . Pi R|,
+//   new l = u + w (s = -1) or Pi (u - w) (s = +1);
+// and the fold of the vertical bond into the column on the right is
+//   T_c[s] = Pi^s D_c Pi^s,  D_c = C_c with odd blocks scaled by tanh(beta Jv),
+// (all-ones bond, t = 0, on the top row). The per-site work is a small GEMM
+// over the CTA's chains: each thread holds a 4 chains x 4 columns register
+// tile and streams C (staged in shared memory, double-buffered) against the
+// chains' vectors (shared memory, chain-minor).
+#include "common.cuh"
+
+namespace tnmc {
+
+namespace {
+
+constexpr int SB = 64;   // chains per CTA
+constexpr int TS = 4;    // chains per thread tile
+constexpr int TC = 4;    // columns per thread tile
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  static __device__ __forceinline__ void load(const float *p, float v[4]) {
+    const float4 x = *reinterpret_cast<const float4 *>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  }
+  static __device__ __forceinline__ void store(float *p, const float v[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Vec4<double> {
+  static __device__ __forceinline__ void load(const double *p, double v[4]) {
+    const double2 x = reinterpret_cast<const double2 *>(p)[0];
+    const double2 y = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+  }
+  static __device__ __forceinline__ void store(double *p, const double v[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+template <int CH>
+struct SampPlan {
+  static constexpr int NCG = CH / TC;           // column groups
+  static constexpr int NT = (SB / TS) * NCG;    // threads
+  static constexpr int LDC = CH + 4;            // padded row of the staged site matrix
+  static constexpr int OWN = (TS + NCG - 1) / NCG;  // chains whose scalars a lane owns
+};
+
+template <typename T, int CH>
+__host__ __device__ constexpr int64_t samp_smem_fixed() {
+  return int64_t(2 * CH * SampPlan<CH>::LDC + 2 * CH * SB) * sizeof(T);
+}
+
+template <typename T, int W>
+__device__ __forceinline__ T gsum(T v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, int CH, bool FORCED>
+__global__ void __launch_bounds__(SampPlan<CH>::NT)
+sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_t *in_spins,
+              uint8_t *out_spins, double *out_logq, double *out_E) {
+  using P = SampPlan<CH>;
+  constexpr int NCG = P::NCG, LDC = P::LDC, OWN = P::OWN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Cs = (T *)smem_raw;                       // 2 x CH x LDC
+  T *Vb = Cs + 2 * CH * LDC;                   // 2 x CH x SB
+  const int bpr = (S + SB - 1) / SB;
+  const int n = lay.order[blockIdx.x / bpr];
+  const int sblk = blockIdx.x % bpr;
+  const RealInfo ri = lay.reals[n];
+  const int L = ri.L;
+  const int WL = (L + 31) / 32;
+  uint32_t *bits = (uint32_t *)(Vb + 2 * CH * SB);   // 2 x SB x WL
+  const int chi = lay.chi;
+  const int tid = threadIdx.x, cg = tid % NCG, sg = tid / NCG;
+  const int lane = tid & 31;
+  const int gbase = lane - cg;                  // first lane of this chain group
+  const float *jr = lay.jr + ri.site_off, *jd = lay.jd + ri.site_off;
+  const T *cache_n = (const T *)lay.cache + ri.site_off * int64_t(chi) * chi;
+  const int2 *bonds_n = lay.bonds + ri.bond_off;
+  T *rs = (T *)lay.samp_scratch + ri.line_off * int64_t(lay.max_samples) * CH;
+  const int64_t L2 = int64_t(L) * L;
+  const T beta = T(lay.beta);
+
+  int sid[TS];        // global chain index in this realization
+  bool act[TS];
+#pragma unroll
+  for (int j = 0; j < TS; ++j) { sid[j] = sblk * SB + sg * TS + j; act[j] = sid[j] < S; }
+
+  // scalars of the chains this lane owns (chain j owned by lane cg == j % NCG)
+  double lq[OWN], en[OWN];
+  int sleft[OWN];
+  uint64_t pw[OWN][4];
+  int64_t pg[OWN];
+#pragma unroll
+  for (int o = 0; o < OWN; ++o) { lq[o] = 0.0; en[o] = 0.0; sleft[o] = 0; pg[o] = -1; }
+
+  uint32_t *bprev = bits, *bcur = bits + SB * WL;
+  for (int e = tid; e < 2 * SB * WL; e += P::NT) bits[e] = 0u;
+  bool any_bad = false;
+  __syncthreads();
+
+  for (int r = 0; r < L; ++r) {
+    const int2 *bd = bonds_n + int64_t(r) * (L + 1);
+    const T *crow = cache_n + int64_t(r) * L * chi * chi;
+    // chain-owner lanes clear this row's bits
+#pragma unroll
+    for (int o = 0; o < OWN; ++o) {
+      const int j = cg + o * NCG;
+      if (j < TS)
+        for (int w = 0; w < WL; ++w) bcur[(sg * TS + j) * WL + w] = 0u;
+    }
+    // ===================== right pass
+    // R_{L-1} = e_0 on the trivial bond L
+    for (int e = tid; e < CH * SB; e += P::NT) Vb[e] = (e < SB) ? T(1) : T(0);
+    int buf = 0;
+    for (int c = L - 2; c >= 0; --c) {
+      // stage D_{c+1}^T: Cs[b][a] = C_{c+1}[a][b] * (t_v on odd blocks)
+      const int2 bl = bd[c + 1], br = bd[c + 2];
+      const T tv = (r > 0) ? Num<T>::tanh_(beta * T(jd[(r - 1) * L + c + 1])) : T(0);
+      T *cs = Cs + buf * CH * LDC;
+      const T *src = crow + int64_t(c + 1) * chi * chi;
+      for (int e = tid; e < CH * CH; e += P::NT) {
+        const int a = e / CH, b = e % CH;
+        T v = (a < chi && b < chi) ? src[a * chi + b] : T(0);
+        if ((a >= bl.x) != (b >= br.x)) v *= tv;
+        cs[b * LDC + a] = v;
+      }
+      __syncthreads();
+      const T *vin = Vb + buf * CH * SB;
+      T acc[TS][TC];
+#pragma unroll
+      for (int j = 0; j < TS; ++j)
+#pragma unroll
+        for (int t = 0; t < TC; ++t) acc[j][t] = T(0);
+      const int Dr = br.x + br.y;
+      for (int b = 0; b < Dr; ++b) {
+        T x[TS], y[TC];
+        Vec4<T>::load(vin + b * SB + sg * TS, x);
+        Vec4<T>::load(cs + b * LDC + cg * TC, y);
+#pragma unroll
+        for (int j = 0; j < TS; ++j)
+#pragma unroll
+          for (int t = 0; t < TC; ++t) acc[j][t] += x[j] * y[t];
+      }
+      // output sign Pi^{s_up(c+1)} on bond c+1, then normalise over the bond
+      T *vout = Vb + (buf ^ 1) * CH * SB;
+#pragma unroll
+      for (int j = 0; j < TS; ++j) {
+        const int sl = sg * TS + j;
+        const int up1 = (r > 0) ? (bprev[sl * WL + ((c + 1) >> 5)] >> ((c + 1) & 31)) & 1 : 0;
+        const int up0 = (r > 0) ? (bprev[sl * WL + (c >> 5)] >> (c & 31)) & 1 : 0;
+        T nrm = 0;
+#pragma unroll
+        for (int t = 0; t < TC; ++t) {
+          const int a = cg * TC + t;
+          if (up1 && a >= bl.x) acc[j][t] = -acc[j][t];
+          nrm += acc[j][t] * acc[j][t];
+        }
+        nrm = gsum<T, NCG>(nrm);
+        const T inv = nrm > T(0) ? T(1) / Num<T>::sqrt_(nrm) : T(0);
+        if (!(nrm > T(0)) && act[j]) any_bad = true;
+        T outv[TC], flp[TC];
+#pragma unroll
+        for (int t = 0; t < TC; ++t) {
+          const int a = cg * TC + t;
+          outv[t] = acc[j][t] * inv;
+          flp[t] = (up0 && a >= bl.x) ? -outv[t] : outv[t];   // input flip of the next step
+        }
+        if (act[j]) Vec4<T>::store(rs + (int64_t(c) * lay.max_samples + sid[j]) * CH + cg * TC, outv);
+#pragma unroll
+        for (int t = 0; t < TC; ++t) vout[(cg * TC + t) * SB + sl] = flp[t];
+      }
+      buf ^= 1;
+    }
+    __syncthreads();
+    // ===================== left pass
+    for (int e = tid; e < CH * SB; e += P::NT) Vb[e] = (e < SB) ? T(1) : T(0);   // l = e_0
+    buf = 0;
+    for (int c = 0; c < L; ++c) {
+      const int2 bl = bd[c], br = bd[c + 1];
+      T *cs = Cs + buf * CH * LDC;
+      const T *src = crow + int64_t(c) * chi * chi;
+      for (int e = tid; e < CH * CH; e += P::NT) {
+        const int a = e / CH, b = e % CH;
+        cs[a * LDC + b] = (a < chi && b < chi) ? src[a * chi + b] : T(0);
+      }
+      // right environment tile of this thread
+      T R[TS][TC];
+#pragma unroll
+      for (int j = 0; j < TS; ++j) {
+        if (c < L - 1 && act[j]) {
+          Vec4<T>::load(rs + (int64_t(c) * lay.max_samples + sid[j]) * CH + cg * TC, R[j]);
+        } else {
+#pragma unroll
+          for (int t = 0; t < TC; ++t) R[j][t] = (c == L - 1 && cg * TC + t == 0) ? T(1) : T(0);
+        }
+      }
+      __syncthreads();
+      const T *vin = Vb + buf * CH * SB;
+      T u[TS][TC], w[TS][TC];
+#pragma unroll
+      for (int j = 0; j < TS; ++j)
+#pragma unroll
+        for (int t = 0; t < TC; ++t) { u[j][t] = T(0); w[j][t] = T(0); }
+      for (int a = 0; a < bl.x; ++a) {
+        T x[TS], y[TC];
+        Vec4<T>::load(vin + a * SB + sg * TS, x);
+        Vec4<T>::load(cs + a * LDC + cg * TC, y);
+#pragma unroll
+        for (int j = 0; j < TS; ++j)
+#pragma unroll
+          for (int t = 0; t < TC; ++t) u[j][t] += x[j] * y[t];
+      }
+      const int Dl = bl.x + bl.y;
+      for (int a = bl.x; a < Dl; ++a) {
+        T x[TS], y[TC];
+        Vec4<T>::load(vin + a * SB + sg * TS, x);
+        Vec4<T>::load(cs + a * LDC + cg * TC, y);
+#pragma unroll
+        for (int j = 0; j < TS; ++j)
+#pragma unroll
+          for (int t = 0; t < TC; ++t) w[j][t] += x[j] * y[t];
+      }
+      // conditional weights, reduced over the column groups
+      T x0[TS], x1[TS];
+#pragma unroll
+      for (int j = 0; j < TS; ++j) {
+        T p0 = 0, p1 = 0;
+#pragma unroll
+        for (int t = 0; t < TC; ++t) {
+          const int b = cg * TC + t;
+          const T pr = (b >= br.x) ? -R[j][t] : R[j][t];
+          p0 += (u[j][t] + w[j][t]) * R[j][t];
+          p1 += (u[j][t] - w[j][t]) * pr;
+        }
+        x0[j] = gsum<T, NCG>(p0);
+        x1[j] = gsum<T, NCG>(p1);
+      }
+      // owners: logit, draw, log q, energy
+      const int i = r * L + c;
+      const T jup = (r > 0) ? T(jd[(r - 1) * L + c]) : T(0);
+      const double jl = (c > 0) ? (double)jr[r * L + c - 1] : 0.0;
+      int sig_own[OWN];
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) {
+        const int j = cg + o * NCG;
+        sig_own[o] = 0;
+        if (j < TS) {
+          const int sl = sg * TS + j;
+          const int up = (r > 0) ? (bprev[sl * WL + (c >> 5)] >> (c & 31)) & 1 : 0;
+          const T rho0 = fabs(x0[j]), rho1 = fabs(x1[j]);
+          T logit;
+          if (rho0 == T(0) && rho1 == T(0)) {
+            logit = T(0);
+            if (act[j]) any_bad = true;
+          } else {
+            logit = Num<T>::log_(rho1) - Num<T>::log_(rho0);
+          }
+          if (r > 0) logit += T(2) * beta * jup * T(up ? 1 : -1);
+          int sgm;
+          if (FORCED) {
+            sgm = act[j] ? in_spins[int64_t(S) * ri.site_off + int64_t(sid[j]) * L2 + i] : 0;
+          } else {
+            const int64_t g = i >> 2;
+            if (g != pg[o]) {
+              const U64x4 ww = philox4x64_10((uint64_t)g, prop_base + (uint64_t)sid[j],
+                                             (uint64_t)n, TAG_SPIN, seed, 0ull);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) pw[o][q] = ww.x[q];
+              pg[o] = g;
+            }
+            const double uu = word_to_uniform(pw[o][i & 3]);
+            const T ls = log_sigmoid<T>(logit);
+            sgm = uu < (double)Num<T>::exp_(ls) ? 1 : 0;
+          }
+          const T lpick = sgm ? log_sigmoid<T>(logit) : log_sigmoid<T>(-logit);
+          lq[o] += (double)lpick;
+          const double sv = sgm ? 1.0 : -1.0;
+          if (c > 0) en[o] -= jl * sv * (double)(sleft[o] ? 1.0 : -1.0);
+          if (r > 0) en[o] -= (double)jup * sv * (up ? 1.0 : -1.0);
+          sleft[o] = sgm;
+          if (sgm) bcur[sl * WL + (c >> 5)] |= 1u << (c & 31);
+          if (act[j]) {
+            const int64_t off = int64_t(S) * ri.site_off + int64_t(sid[j]) * L2 + i;
+            if (!FORCED) out_spins[off] = (uint8_t)sgm;
+            if (lay.dbg_logits) lay.dbg_logits[off] = (float)logit;
+          }
+          sig_own[o] = sgm;
+        }
+      }
+      // broadcast the decisions to the chain group, update the left environment
+      T *vout = Vb + (buf ^ 1) * CH * SB;
+#pragma unroll
+      for (int j = 0; j < TS; ++j) {
+        const int src = gbase + (j % NCG);
+        const int sgm = __shfl_sync(0xffffffffu, sig_own[j / NCG], src);
+        T nv[TC];
+        T nrm = 0;
+#pragma unroll
+        for (int t = 0; t < TC; ++t) {
+          const int b = cg * TC + t;
+          nv[t] = sgm ? ((b >= br.x) ? -(u[j][t] - w[j][t]) : (u[j][t] - w[j][t]))
+                      : (u[j][t] + w[j][t]);
+          nrm += nv[t] * nv[t];
+        }
+        nrm = gsum<T, NCG>(nrm);
+        const T inv = nrm > T(0) ? T(1) / Num<T>::sqrt_(nrm) : T(0);
+        if (!(nrm > T(0)) && act[j]) any_bad = true;
+#pragma unroll
+        for (int t = 0; t < TC; ++t) vout[(cg * TC + t) * SB + sg * TS + j] = nv[t] * inv;
+      }
+      buf ^= 1;
+    }
+    __syncthreads();
+    uint32_t *tmp = bprev; bprev = bcur; bcur = tmp;
+  }
+  // results
+#pragma unroll
+  for (int o = 0; o < OWN; ++o) {
+    const int j = cg + o * NCG;
+    if (j < TS && act[j]) {
+      out_logq[int64_t(n) * S + sid[j]] = lq[o];
+      out_E[int64_t(n) * S + sid[j]] = en[o];
+    }
+  }
+  if (any_bad) set_flag(lay.flags, n, FLAG_NUMERIC);
+}
+
+}  // namespace
+
+template <typename T, int CH, bool FORCED>
+static cudaError_t launch_samp_t(const Layout &lay, int S, uint64_t seed, uint64_t base,
+                                 const uint8_t *in, uint8_t *out, double *lq, double *E,
+                                 cudaStream_t st) {
+  using P = SampPlan<CH>;
+  const int WL = (lay.L_max + 31) / 32;
+  const int64_t smem = samp_smem_fixed<T, CH>() + int64_t(2) * SB * WL * 4;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(sample_kernel<T, CH, FORCED>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int bpr = (S + SB - 1) / SB;
+  sample_kernel<T, CH, FORCED><<<lay.n_real * bpr, P::NT, smem, st>>>(lay, S, seed, base, in, out,
+                                                                      lq, E);
+  return cudaGetLastError();
+}
+
+template <bool FORCED>
+static cudaError_t launch_samp(const Layout &lay, int prec, int CH, int S, uint64_t seed,
+                               uint64_t base, const uint8_t *in, uint8_t *out, double *lq,
+                               double *E, cudaStream_t st) {
+  if (prec == 0) {
+    switch (CH) {
+      case 8: return launch_samp_t<double, 8, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+      case 16: return launch_samp_t<double, 16, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+      case 32: return launch_samp_t<double, 32, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+      case 64: return launch_samp_t<double, 64, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+    }
+  } else {
+    switch (CH) {
+      case 8: return launch_samp_t<float, 8, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+      case 16: return launch_samp_t<float, 16, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+      case 32: return launch_samp_t<float, 32, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+      case 64: return launch_samp_t<float, 64, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_propose(const Layout &lay, int prec, int CH, int S, uint64_t seed,
+                           uint64_t base, uint8_t *spins, double *lq, double *E,
+                           cudaStream_t st) {
+  return launch_samp<false>(lay, prec, CH, S, seed, base, nullptr, spins, lq, E, st);
+}
+
+cudaError_t launch_score(const Layout &lay, int prec, int CH, int S, const uint8_t *spins,
+                         double *lq, double *E, cudaStream_t st) {
+  return launch_samp<true>(lay, prec, CH, S, 0, 0, spins, nullptr, lq, E, st);
+}
+
+int64_t sampler_smem_bytes(int prec, int CH, int L_max) {
+  const int WL = (L_max + 31) / 32;
+  const int64_t extra = int64_t(2) * SB * WL * 4;
+  if (prec == 0) {
+    switch (CH) {
+      case 8: return samp_smem_fixed<double, 8>() + extra;
+      case 16: return samp_smem_fixed<double, 16>() + extra;
+      case 32: return samp_smem_fixed<double, 32>() + extra;
+      case 64: return samp_smem_fixed<double, 64>() + extra;
+    }
+  } else {
+    switch (CH) {
+      case 8: return samp_smem_fixed<float, 8>() + extra;
+      case 16: return samp_smem_fixed<float, 16>() + extra;
+      case 32: return samp_smem_fixed<float, 32>() + extra;
+      case 64: return samp_smem_fixed<float, 64>() + extra;
+    }
+  }
+  return -1;
+}
+
+}  // namespace tnmc

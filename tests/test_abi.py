@@ -1,0 +1,72 @@
+"""The C-ABI library loads on a machine without a GPU and exports every entry
+point include/tnmc.h declares; host-only calls (sizes, argument checks) work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2509_19006_b300 import build
+    build.build()
+    import paper_2509_19006_b300 as P
+    return P
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^[A-Za-z_][\w \*]*?\b(tnmc_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(P):
+    lib = ctypes.CDLL(P.LIB_PATH)
+    names = declared_functions()
+    assert "tnmc_build_envs" in names and "tnmc_propose" in names and "tnmc_mh_step" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(P.EXPORTED) <= set(names)
+
+
+def test_workspace_size_host_only(P):
+    small = P.workspace_size([16], 16, 1.0, P.TNMC_FP64, 1000)
+    assert small > 0
+    cache, env, samp = P.layout_info([256] * 64, 64, 3.0, P.TNMC_FP32, 256)
+    assert cache == 64 * 256 * 256 * 64 * 64 * 4          # one chi x chi float matrix per site
+    assert samp == 256 * 64 * 256 * 64 * 4                # right environments of every chain
+    # float64 doubles the cache
+    c64, _, _ = P.layout_info([256] * 64, 64, 3.0, P.TNMC_FP64, 256)
+    assert c64 == 2 * cache
+
+
+@pytest.mark.parametrize("args", [
+    ([16], 0, 1.0, 1, 4),        # chi < 1
+    ([16], 65, 1.0, 1, 4),       # chi > 64
+    ([0], 4, 1.0, 1, 4),         # L < 1
+    ([16], 4, -1.0, 1, 4),       # beta < 0
+    ([16], 4, float("nan"), 1, 4),
+    ([16], 4, 1.0, 9, 4),        # unknown precision
+    ([16], 4, 1.0, 1, 0),        # max_samples < 1
+])
+def test_argument_checks(P, args):
+    with pytest.raises(P.TnmcError) as e:
+        P.workspace_size(*args)
+    assert e.value.status == 1
+
+
+def test_reserved_precisions_unsupported(P):
+    with pytest.raises(P.TnmcError) as e:
+        P.workspace_size([16], 4, 1.0, P.TNMC_BF16, 4)
+    assert e.value.status == 7
+
+
+def test_status_strings(P):
+    for code in range(8):
+        assert P.status_string(code)

@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+float64 mode: log Z and bond spectra to ~1e-10, proposals (spins, energies)
+bit-exact, log q to 1e-9, MH accepts bit-exact; a configuration may differ only
+at a draw whose uniform lies within 1e-9 of the oracle's probability (counted).
+float32 mode: log Z per site to 1e-6 and a teacher-forced audit of every draw.
+A configuration whose draws land near a tie at a truncation cut is not compared
+bit for bit (the kept subspace is then decided by rounding); the cases below
+have wide cut gaps.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bmps, mh, philox, sampler  # noqa: E402
+from oracle.ising import energy  # noqa: E402
+import parity  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_19006_b300 import build
+    build.build()
+    import paper_2509_19006_b300 as P
+    return P
+
+
+def _run(P, Ls, chi, beta, prec, kind, S, seed=42, prop_base=0, diag=False):
+    reals = parity.realizations(Ls, kind)
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, prec, max_samples=max(S, 1))
+    d = t.set_diagnostics(S=S, logits=True, spectra=True, rowinfo=True) if diag else None
+    t.build_envs(J)
+    lz = t.log_z().cpu().numpy()
+    props = t.propose(S, seed, prop_base)
+    torch.cuda.synchronize()
+    st, flags = t.device_status()
+    return t, reals, lz, props, d, st, flags
+
+
+CASES_FP64 = [
+    ([2], 2, 1.0, "pmj"),
+    ([3], 2, 0.7, "pmj"),
+    ([4], 4, 1.5, "gauss"),
+    ([5], 3, 1.0, "pmj"),       # truncated, odd chi
+    ([8], 4, 2.0, "pmj"),       # truncated
+    ([6, 3, 7], 8, 1.0, "gauss"),   # uneven batch, exact chi
+    ([16], 16, 1.0, "pmj"),     # the L=16, chi=16, beta=1 workload
+    ([1, 2], 1, 0.5, "pmj"),    # degenerate: L=1 and chi=1
+]
+
+
+@pytest.mark.parametrize("Ls,chi,beta,kind", CASES_FP64)
+def test_fp64_log_z_spectra_and_proposals(P, Ls, chi, beta, kind):
+    S = 70  # two CTAs of chains, the second one ragged
+    t, reals, lz, props, (lg, sp, ri), st, flags = _run(P, Ls, chi, beta, "fp64", kind, S, diag=True)
+    assert st == 0 and not flags.any()
+    envs = parity.oracle_envs(reals, beta, chi)
+    spins = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
+    lq = props.logq.cpu().numpy()
+    E = props.E.cpu().numpy()
+    sp = sp.cpu().numpy()
+    ri = ri.cpu().numpy().reshape(-1, 6)
+    bo = ro = 0
+    total_bd = 0
+    for n, (L, (Jh, Jv), rows) in enumerate(zip(Ls, reals, envs)):
+        o_lz = bmps.log_z(rows)
+        assert abs(lz[n] - o_lz) < 1e-10 * max(1.0, abs(o_lz)), (n, lz[n], o_lz)
+        # per-row log scale is a gauge-dependent quantity; compare the spectra instead
+        for r in range(L):
+            for c in range(1, L):
+                o_s = rows[r].spectra[c - 1]
+                g_s = sp[(bo + r * (L + 1) + c) * chi:(bo + r * (L + 1) + c + 1) * chi]
+                gap = rows[r].cut_gap[c - 1]
+                keep = o_s > 1e-7
+                if gap > 1e-6:
+                    np.testing.assert_allclose(g_s[:keep.sum()], o_s[keep], rtol=1e-8, atol=1e-12)
+        n_eq, n_bd = parity.compare_proposals(rows, Jh, Jv, beta, 42, 0, n, spins[n], lq[n], E[n])
+        total_bd += n_bd
+        bo += L * (L + 1)
+        ro += L
+    assert total_bd <= 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_score_matches_propose(P, prec):
+    Ls, chi, beta = [9, 6], 4, 1.3
+    S = 64
+    t, reals, lz, props, _, st, _ = _run(P, Ls, chi, beta, prec, "gauss", S)
+    lq2, E2 = t.score(props.spins, S)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    np.testing.assert_allclose(lq2.cpu().numpy(), props.logq.cpu().numpy(), rtol=0, atol=tol * 100)
+    np.testing.assert_array_equal(E2.cpu().numpy(), props.E.cpu().numpy())
+
+
+def test_fp64_energies_exact_and_oracle_scoring(P):
+    Ls, chi, beta, S = [12], 6, 2.0, 128
+    t, reals, lz, props, _, _, _ = _run(P, Ls, chi, beta, "fp64", "pmj", S, prop_base=12345)
+    Jh, Jv = reals[0]
+    sig = parity.split_spins(props.spins.cpu().numpy(), Ls, S)[0]
+    np.testing.assert_array_equal(props.E.cpu().numpy()[0], energy(Jh, Jv, sig))
+    rows = bmps.build_envs(Jh, Jv, beta, chi)
+    o_lq, _, _ = sampler.score(rows, Jh, Jv, beta, sig)
+    np.testing.assert_allclose(props.logq.cpu().numpy()[0], o_lq, rtol=0, atol=1e-9)
+
+
+def test_fp64_mh_chain_bit_exact(P):
+    Ls, chi, beta, S = [8, 5], 4, 1.0, 200
+    reals = parity.realizations(Ls, "pmj")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    t.build_envs(J)
+    state = t.mh_init(seed=7)
+    s0 = parity.split_spins(state.spins.cpu().numpy(), Ls, 1)
+    s0_lq, s0_E = state.logq.cpu().numpy().copy(), state.E.cpu().numpy().copy()
+    envs = parity.oracle_envs(reals, beta, chi)
+    for n, (L, (Jh, Jv), rows) in enumerate(zip(Ls, reals, envs)):
+        np.testing.assert_array_equal(s0[n][0], philox.init_spins(L, n, 7))
+        o_lq, o_E, _ = sampler.score(rows, Jh, Jv, beta, s0[n])
+        assert s0_E[n] == o_E[0]
+        assert abs(s0_lq[n] - o_lq[0]) < 1e-9
+    total_acc = 0
+    for step in range(2):
+        base = 1000 * step
+        props = t.propose(S, seed=7, prop_base=base)
+        acc = t.mh_step(props, state, seed=7).cpu().numpy()
+        psig = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
+        plq, pE = props.logq.cpu().numpy(), props.E.cpu().numpy()
+        for n, (L, (Jh, Jv), rows) in enumerate(zip(Ls, reals, envs)):
+            st_in = (s0[n][0], s0_lq[n], s0_E[n])
+            # the oracle chain on the GPU's own proposals: same accept decisions
+            (o_sig, o_lq, o_E), o_acc, o_lr, o_u = mh.chain(st_in, (psig[n], plq[n], pE[n]), beta, 7, base, n)
+            near = np.abs(np.log(o_u) - o_lr) < 1e-9
+            assert np.array_equal(acc[n][~near], o_acc[~near])
+            total_acc += int(acc[n].sum())
+            s0[n][0], s0_lq[n], s0_E[n] = o_sig, o_lq, o_E
+        torch.cuda.synchronize()
+        g_sig = parity.split_spins(state.spins.cpu().numpy(), Ls, 1)
+        for n in range(len(Ls)):
+            np.testing.assert_array_equal(g_sig[n][0], s0[n][0])
+            assert state.E.cpu().numpy()[n] == s0_E[n]
+    assert state.n_accept.cpu().numpy().sum() == total_acc
+    assert total_acc > 0
+
+
+@pytest.mark.parametrize("Ls,chi,beta,kind", [([10, 7], 8, 2.0, "pmj"), ([8, 6], 16, 2.0, "pmj"),
+                                             ([12], 8, 1.0, "gauss"), ([10], 32, 2.0, "pmj")])
+def test_fp32_log_z_and_draw_audit(P, Ls, chi, beta, kind):
+    """float32 mode against the float64 oracle.
+
+    |d log Z| / L^2 <= 1e-6 (cases whose cut gaps are wide); energies exact;
+    teacher-forced audit: every draw agrees with the oracle's float64
+    conditional unless the uniform lies within 2e-3 of its probability.
+    log q: float32 rounding of the cache alone already moves log q by ~1e-3
+    at beta = 2 (test_fp32_storage_bound in test_precision_model.py), so the
+    bound here is 1e-2, not the float64 1e-9.
+    """
+    S = 64
+    t, reals, lz, props, (lg, _, _), st, flags = _run(P, Ls, chi, beta, "fp32", kind, S, diag=True)
+    assert st == 0
+    envs = parity.oracle_envs(reals, beta, chi, t.cutoff)   # the same truncation rule
+    spins = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
+    lq = props.logq.cpu().numpy()
+    for n, (L, (Jh, Jv), rows) in enumerate(zip(Ls, reals, envs)):
+        assert min(g for r in rows for g in r.cut_gap) > 1e-2
+        assert abs(lz[n] - bmps.log_z(rows)) / (L * L) < 1e-6
+        o_lq, o_E, o_lg = sampler.score(rows, Jh, Jv, beta, spins[n])
+        np.testing.assert_array_equal(props.E.cpu().numpy()[n], o_E)
+        assert np.abs(lq[n] - o_lq).max() < 1e-2
+        u = philox.spin_uniforms(L, np.arange(S, dtype=np.uint64), n, 42)
+        p = sampler.sigmoid(o_lg)
+        want = (u < p).astype(np.uint8)
+        got = spins[n].reshape(S, -1)
+        band = np.abs(u - p) < 2e-3
+        assert np.array_equal(got[~band], want[~band])
+
+
+def test_bad_couplings_flagged(P):
+    Ls = [4, 5]
+    reals = parity.realizations(Ls, "pmj")
+    Jnp = parity.packed_J(reals)
+    Jnp[16 + 3, 2] = 7.0           # realization 1, site (0, 3): right != left of (0, 4)
+    t = P.TNMC(Ls, 4, 1.0, "fp32", max_samples=8)
+    t.build_envs(torch.from_numpy(Jnp).cuda())
+    st, flags = t.device_status()
+    assert flags[0] == 0 and flags[1] & P.FLAG_BAD_COUPLINGS
+    assert st == 1   # TNMC_ERR_ARG
+
+
+def test_argument_errors(P):
+    with pytest.raises(P.TnmcError):
+        P.TNMC([8], 65, 1.0, "fp32", max_samples=4)           # chi > 64
+    with pytest.raises(P.TnmcError):
+        P.TNMC([8], 4, 1.0, "bf16", max_samples=4)            # not implemented
+    t = P.TNMC([8], 4, 1.0, "fp32", max_samples=4)
+    with pytest.raises(P.TnmcError) as e:
+        t.propose(2, 1)                                       # before build
+    assert e.value.status == 6
+    reals = parity.realizations([8], "pmj")
+    t.build_envs(torch.from_numpy(parity.packed_J(reals)).cuda())
+    with pytest.raises(P.TnmcError):
+        t.propose(5, 1)                                       # S > max_samples

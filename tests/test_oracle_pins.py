@@ -176,7 +176,12 @@ def test_cache_rows_equal_exact_boundary_functions():
     bits = ((ys[:, None] >> np.arange(L)[None, :]) & 1)
     for r in range(L):
         got = np.array([bmps.contract_row(rows[r], b) for b in bits])
-        np.testing.assert_allclose(got, F[r], rtol=0, atol=1e-11 * np.abs(F[r]).max())
+        top = F[r].max()
+        # F_r itself to 1e-10 of its largest value (the 1e-12 singular-value cutoff
+        # leaves configurations far below the largest one unresolved)
+        np.testing.assert_allclose(np.exp(got - top), np.exp(F[r] - top), rtol=0, atol=1e-10)
+        big = F[r] > top - 10.0
+        np.testing.assert_allclose(got[big], F[r][big], rtol=0, atol=1e-9)
 
 
 # ---------------------------------------------------------------- conditionals / q
@@ -323,3 +328,17 @@ def test_mh_accept_rule_matches_definition():
         if acc[k]:
             lq, E = P_lq[k], P_E[k]
     assert lq == lq_end and E == E_end
+
+
+def test_truncation_threshold_is_needed_and_exact_against_transfer_matrix():
+    """Reading of Sec. 1's truncation threshold, pinned to the exact row transfer matrix.
+
+    L = 18, beta = 3: with the relative cutoff the bMPS log Z equals the exact
+    one to 1e-7; keeping numerically-zero singular values (cutoff 0) lets noise
+    grow and misses it by > 1e-4 although no physical weight was discarded.
+    """
+    L, beta = 18, 3.0
+    Jh, Jv = draw_bonds(L, 1000, "pmj")
+    lz = exact.transfer_log_z(Jh, Jv, beta)
+    assert abs(bmps.log_z(bmps.build_envs(Jh, Jv, beta, 32, 1e-12)) - lz) < 1e-7
+    assert abs(bmps.log_z(bmps.build_envs(Jh, Jv, beta, 32, 0.0)) - lz) > 1e-4
