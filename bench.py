@@ -1,0 +1,376 @@
+"""Benchmark of the batched TNMC hot path on B300 (one JSON line on stdout).
+
+A step is one pass of the whole hot path over one batch: coupling ingest and
+the boundary-MPS environments of every realization, S proposals per
+realization with log q and energies, and the independence Metropolis-Hastings
+scan (Sec. 3.2-3.4, Eq. 10). Default workload: 64 +-J realizations at L = 256,
+beta = 3, chi = 64, S = 256 (the accepted-samples/s workload).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|fp32|mixed]
+                    [--impl ours|reference] [--workload L256]
+
+Under torchrun (N > 1) each rank runs its own batch of the same size with its
+own disorder seeds (weak scaling, no collective on the data path); rank 0
+prints the line with the whole-job throughput (the slowest rank's time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import SAMPLING_SEED, config  # noqa: E402
+
+METRIC = "accepted samples/s at L=256,chi=64 (end to end: environments + proposals + MH)"
+FP64_NOMINAL_GFLOPS = 1250.0          # B300 float64 (recipe table)
+FP32_PEAK_GFLOPS = 148 * 128 * 2 * 2.032  # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[2 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------- oracle arm
+def oracle_sample(wl, seconds: float = 15.0):
+    """Time the FP64 oracle on a bounded sample of the workload.
+
+    Realization 0: the environment rows are built from the bottom up until
+    `seconds` have elapsed; the per-row cost of the last half of those rows is
+    extrapolated to all L rows. Proposals are not timed: the environment build
+    dominates the oracle's time, so this is an upper bound on its throughput.
+    """
+    from oracle import bmps
+    L, chi, beta = wl.Ls[0], wl.chi, wl.beta
+    Jh, Jv = wl.realization(0)
+    t0 = time.perf_counter()
+    mps, lam = bmps.bottom_row_mps(Jh[L - 1], beta)
+    times = []
+    for r in range(L - 1, -1, -1):
+        ts = time.perf_counter()
+        if r < L - 1:
+            mpo, sc = bmps.row_mpo(Jh[r], Jv[r], beta)
+            mps = bmps.multiply(mpo, mps)
+        mps = bmps.compress(mps, chi)[0]
+        times.append(time.perf_counter() - ts)
+        if time.perf_counter() - t0 > seconds and len(times) >= 4:
+            break
+    steady = times[len(times) // 2:]
+    per_row = sum(steady) / len(steady)
+    return per_row * L, len(times), time.perf_counter() - t0
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(wl, seconds=args.ref_seconds / 3)
+    for _ in range(args.steps):
+        t_real, rows_done, wall = oracle_sample(wl, seconds=args.ref_seconds)
+        # the oracle computes the same method; its acceptance is the method's (given)
+        vals.append(wl.S * args.ref_acceptance / t_real)
+    v = float(np.mean(vals))
+    sample = (f"realization 0 of {wl.name}: bottom {rows_done} environment rows timed, "
+              f"per-row cost extrapolated to all {wl.Ls[0]} rows; proposals not timed; "
+              f"acceptance {args.ref_acceptance} taken from the GPU run")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "accepted/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "realizations": 1},
+            "cpu_baseline": {"value": v, "unit": "accepted/s", "cores": cpu_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "accepted/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------- our arm
+def run_ours(args, wl):
+    import torch
+    import paper_2509_19006_b300 as P
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    # weak scaling: every rank a full batch with its own disorder seeds
+    wl.base_seed = wl.base_seed + rank * 100000
+    Jhost = torch.from_numpy(wl.packed_J()).pin_memory()
+    J = Jhost.to(dev)
+    S = wl.S
+    t = P.TNMC(wl.Ls, wl.chi, wl.beta, args.prec, max_samples=S, device=dev, cutoff=args.cutoff)
+    stream = t.stream
+    props = t.alloc_proposals(S)
+    state = None
+    acc = torch.empty((wl.n_real, S), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
+    logz = torch.empty(wl.n_real, dtype=torch.float64, device=dev)
+
+    def step(base):
+        nonlocal state
+        t.build_envs(J)
+        t.log_z(out=logz)
+        t.propose(S, SAMPLING_SEED, base, out=props)
+        if state is None:
+            state = t.mh_init(SAMPLING_SEED)
+        t.mh_step(props, state, SAMPLING_SEED, accept=acc)
+
+    # warm-up (the first one also gathers the algorithmic flop count of the build)
+    _, _, rowinfo = t.set_diagnostics(rowinfo=True)
+    for w in range(args.warmup):
+        step(1_000_000 * (w + 1))
+        if w == 0:
+            torch.cuda.synchronize()
+            ri = rowinfo.cpu().numpy().reshape(-1, 14)
+            flops_env = float(ri[:, 13].sum())
+            dmean = float(ri[:, 5].mean())
+            t.set_diagnostics()
+    torch.cuda.synchronize()
+    st, flags = t.device_status()
+    if st != 0:
+        print(f"warning: device status {st}, flags {np.unique(flags)}", file=sys.stderr)
+
+    # ---------------- device-resident timed region
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    env_ms, step_ms, accepted = [], [], 0
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    n_acc0 = state.n_accept.clone()
+    t_all0 = ev(); t_all1 = ev()
+    with torch.cuda.stream(stream):
+        t_all0.record(stream)
+        for k in range(args.steps):
+            flush.zero_()
+            e0, e1, e2 = ev(), ev(), ev()
+            e0.record(stream)
+            t.build_envs(J)
+            e1.record(stream)
+            t.log_z(out=logz)
+            t.propose(S, SAMPLING_SEED, 10_000_000 * (k + 1), out=props)
+            t.mh_step(props, state, SAMPLING_SEED, accept=acc)
+            e2.record(stream)
+            env_ms.append((e0, e1))
+            step_ms.append((e0, e2))
+        t_all1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    accepted = int((state.n_accept - n_acc0).sum().item())
+    env_t = [a.elapsed_time(b) for a, b in env_ms]
+    step_t = [a.elapsed_time(b) for a, b in step_ms]
+    total_ms = t_all0.elapsed_time(t_all1)   # includes the L2 flushes between steps
+    my_ms = sum(step_t)
+
+    # ---------------- end to end through the public API with host buffers
+    h_acc = torch.empty((wl.n_real, S), dtype=torch.uint8).pin_memory()
+    h_nacc = torch.empty(wl.n_real, dtype=torch.int64).pin_memory()
+    h_logz = torch.empty(wl.n_real, dtype=torch.float64).pin_memory()
+    e2e_acc = 0
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            n0 = state.n_accept.clone()
+            J.copy_(Jhost, non_blocking=True)
+            t.build_envs(J)
+            t.log_z(out=logz)
+            t.propose(S, SAMPLING_SEED, 20_000_000 * (k + 1), out=props)
+            t.mh_step(props, state, SAMPLING_SEED, accept=acc)
+            h_acc.copy_(acc, non_blocking=True)
+            h_nacc.copy_(state.n_accept - n0, non_blocking=True)
+            h_logz.copy_(logz, non_blocking=True)
+            stream.synchronize()
+            e2e_acc += int(h_nacc.sum())
+    e2e_s = time.perf_counter() - w0
+    h2d = Jhost.numel() * 4
+    d2h = h_acc.numel() + h_nacc.numel() * 8 + h_logz.numel() * 8
+
+    # ---------------- gather over ranks (max time, summed work)
+    vec = torch.tensor([my_ms, float(accepted), e2e_s, float(e2e_acc)], dtype=torch.float64, device=dev)
+    if world > 1:
+        mx = vec.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = vec.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        my_ms_all, accepted_all, e2e_s_all, e2e_acc_all = mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
+    else:
+        my_ms_all, accepted_all, e2e_s_all, e2e_acc_all = my_ms, accepted, e2e_s, e2e_acc
+
+    if rank == 0:
+        peaks = load_peaks()
+        env_avg_s = sum(env_t) / len(env_t) / 1e3
+        achieved = flops_env / env_avg_s / 1e9
+        if args.prec == "fp32":
+            peak, peak_src = FP32_PEAK_GFLOPS, "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"
+        else:
+            peak, peak_src = FP64_NOMINAL_GFLOPS, "nominal float64 rate (recipe table, not measured)"
+        proposals = wl.n_real * S * args.steps
+        cpu = None
+        if world == 1 and args.cpu_baseline:
+            t_real, rows_done, _ = oracle_sample(wl, seconds=args.ref_seconds)
+            acc_rate = accepted / proposals
+            cpu = {"value": S * acc_rate / t_real, "unit": "accepted/s", "cores": cpu_cores(),
+                   "kind": "oracle",
+                   "sample": (f"FP64 oracle, realization 0 of {wl.name}: bottom {rows_done} environment "
+                              f"rows timed and extrapolated to {wl.Ls[0]} rows (proposals not timed); "
+                              f"acceptance taken from this run ({acc_rate:.4f})")}
+        line = {
+            "metric": METRIC,
+            "value": accepted_all / (my_ms_all / 1e3),
+            "unit": "accepted/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": my_ms_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f64 build + f32 sampling"}[args.prec],
+            "data": "synthetic +-J disorder (p = 1/2), seeded",
+            "config": {"workload": wl.name, "L": wl.Ls[0], "chi": wl.chi, "beta": wl.beta,
+                       "realizations_per_gpu": wl.n_real, "samples_per_realization": S,
+                       "precision": args.prec, "cutoff": t.cutoff,
+                       "l2": "flushed (256 MB write) before every timed step; environment cache >> L2"},
+            "acceptance": accepted / proposals,
+            "proposals_per_s": proposals * world / (my_ms_all / 1e3),
+            "env_build_ms": env_avg_s * 1e3,
+            "bond_dim_mean": dmean,
+            "roofline": {"kernel": "env_build_kernel (boundary-MPS build)", "bound": "alu",
+                         "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": None,
+                         "algorithmic_flops_per_launch": flops_env},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_acc_all / e2e_s_all, "unit": "accepted/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * (2 + 1 + 1 + 1),
+            "clocks": clk,
+            "hbm_gbs_measured": peaks.get("hbm_gbs"),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_env_once(args, wl):
+    """Build the environments of the workload once (a target for profiler captures)."""
+    import torch
+    import paper_2509_19006_b300 as P
+    J = torch.from_numpy(wl.packed_J()).cuda()
+    t = P.TNMC(wl.Ls, wl.chi, wl.beta, args.prec, max_samples=wl.S, cutoff=args.cutoff)
+    t.build_envs(J)
+    lz = t.log_z()
+    torch.cuda.synchronize()
+    st, flags = t.device_status()
+    print(json.dumps({"workload": wl.name, "precision": args.prec, "status": int(st),
+                      "log_z_0": float(lz[0].item())}), flush=True)
+    if st != 0 and st != 4:
+        sys.exit(1)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp64", "fp32", "mixed"], default="fp64")
+    ap.add_argument("--workload", default="L256")
+    ap.add_argument("--cutoff", type=float, default=0.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-acceptance", type=float, default=1.0)
+    ap.add_argument("--env-once", action="store_true",
+                    help="build the environments once and exit (for profiler captures)")
+    args = ap.parse_args()
+    wl = config(args.workload)
+    if args.env_once:
+        run_env_once(args, wl)
+    elif args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

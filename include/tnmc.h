@@ -66,7 +66,9 @@ typedef enum {
   TNMC_FP64 = 0,   /* all tensor arithmetic and the cache in float64 */
   TNMC_FP32 = 1,   /* all tensor arithmetic and the cache in float32 */
   TNMC_TF32 = 2,   /* reserved: tensor-core TF32 contractions */
-  TNMC_BF16 = 3    /* reserved: tensor-core BF16 contractions */
+  TNMC_BF16 = 3,   /* reserved: tensor-core BF16 contractions */
+  TNMC_MIXED = 4   /* float64 environment build (QR / SVD truncation, carried between
+                      rows in float64), float32 cache and float32 sampling contractions */
 } tnmc_prec;
 
 /* Device flags (bit mask per realization) reported by tnmc_get_device_status. */
@@ -84,7 +86,7 @@ typedef struct {
   double cutoff;         /* relative singular-value cutoff of the truncation (Sec. 1's
                             truncation threshold): at each bond keep the chi largest
                             singular values that exceed cutoff * (largest). <= 0 selects
-                            the default of the precision: 1e-12 (FP64), 1e-6 (FP32).
+                            the default of the precision: 1e-12 (FP64, MIXED), 1e-6 (FP32).
                             Numerically-zero singular values must be dropped: their
                             noise directions grow under the next rows' transfer MPOs. */
 } tnmc_config;
@@ -173,10 +175,15 @@ tnmc_status tnmc_mh_step(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
  * d_spectra: float64 [sum_n L_n (L_n + 1) chi] of build_envs: at row r,
  *            bond b (between sites b-1 and b), the kept singular values
  *            divided by the largest, in decreasing order, zero padded;
- * d_rowinfo: float64 [sum_n L_n * 6] of build_envs: per row (log of the
+ * d_rowinfo: float64 [sum_n L_n * 14] of build_envs: per row (log of the
  *            2-norm of F_r, smallest relative gap s_kept/s_dropped - 1 at a
  *            cut, largest discarded weight, bonds where values were dropped,
- *            largest bond dimension, mean bond dimension). */
+ *            largest bond dimension, mean bond dimension, Jacobi SVDs run,
+ *            mean Jacobi sweeps per SVD, then SM cycles spent in: MPO
+ *            application + R handling, QR + Q formation, Theta product +
+ *            setup, Jacobi, selection + stores, and the row's algorithmic
+ *            flops: textbook counts of its QRs (2mn^2 - 2n^3/3, twice for Q),
+ *            SVDs (4a^2b + 8ab^2 + 9b^3, Golub-Reinsch) and products). */
 tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spectra,
                                  double *d_rowinfo);
 

@@ -20,6 +20,5 @@ What it computes is the method itself, step by step, in float64 numpy:
 * ``exact``   - brute-force enumeration (Eq. 2-4) and the exact row transfer
                 matrix, the references the oracle is pinned against.
 
-Readings of points the paper leaves open are listed in the design doc and repeated
-in each function's docstring.
+Each function's docstring states how it reads the points the paper leaves open.
 """

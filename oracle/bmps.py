@@ -17,7 +17,7 @@ Site tensors are float64 arrays (D_left, 2, D_right), index order
 [left, physical, right] as in Sec. 3.2; the physical index is the spin bit
 (0: s = -1, 1: s = +1).
 
-Readings of points the paper leaves open (all listed in the design doc):
+Readings of points the paper leaves open:
 * compress = a left-to-right QR sweep (left-canonical form), then a
   right-to-left SVD sweep keeping, at each bond, the singular values that are
   among the chi largest AND above cutoff * (largest) -- the "truncation

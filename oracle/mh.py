@@ -5,7 +5,7 @@ min(1, q(s) P(s') / (q(s') P(s))) = min(1, exp(log r)) with
 
     log r = (-beta E(s') - log q(s')) - (-beta E(s) - log q(s)).
 
-Readings: one chain per realization; proposals are consumed in
+Readings of the paper: one chain per realization; proposals are consumed in
 their id order; the accept test is u < exp(log r) taken as log u < log r in
 float64, u the Philox uniform of the proposal (stream 1). The initial state is
 a uniformly random configuration (stream 2) scored by the proposal's own q.

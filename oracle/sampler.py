@@ -11,7 +11,7 @@ For row r, given the rows above (``s_up`` = row r-1):
   +1 with probability sigmoid(logit); log q gains log sigmoid(+-logit) (Eq. 9);
   l <- l M_c[:, s, :] divided by its 2-norm.
 
-Reading: for row 0 there is no row above; the fold uses the all-ones
+Reading of the paper: for row 0 there is no row above; the fold uses the all-ones
 matrix (J = 0) and the up-field is 0. The draw is: spin +1 iff u < sigmoid(logit)
 with u the Philox uniform of that site (``philox.py``). If rho_0 = rho_1 = 0
 the conditional is undefined and the call raises.

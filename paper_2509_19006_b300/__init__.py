@@ -17,8 +17,9 @@ from typing import List, Optional, Sequence
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtnmc.so")
 
-TNMC_FP64, TNMC_FP32, TNMC_TF32, TNMC_BF16 = 0, 1, 2, 3
-PRECISIONS = {"fp64": TNMC_FP64, "fp32": TNMC_FP32, "tf32": TNMC_TF32, "bf16": TNMC_BF16}
+TNMC_FP64, TNMC_FP32, TNMC_TF32, TNMC_BF16, TNMC_MIXED = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": TNMC_FP64, "fp32": TNMC_FP32, "tf32": TNMC_TF32, "bf16": TNMC_BF16,
+              "mixed": TNMC_MIXED}
 FLAG_BAD_COUPLINGS, FLAG_NUMERIC, FLAG_TIMEOUT = 1, 2, 4
 
 EXPORTED = [
@@ -139,7 +140,7 @@ class ChainState:
 class TNMC:
     """A handle on the library for one batch of realizations on one CUDA device."""
 
-    DEFAULT_CUTOFF = {TNMC_FP64: 1e-12, TNMC_FP32: 1e-6}
+    DEFAULT_CUTOFF = {TNMC_FP64: 1e-12, TNMC_FP32: 1e-6, TNMC_MIXED: 1e-12}
 
     def __init__(self, Ls: Sequence[int], chi: int, beta: float, prec: str | int = "fp32",
                  max_samples: int = 256, device="cuda:0", stream=None, cutoff: float = 0.0):
@@ -240,7 +241,7 @@ class TNMC:
         t = self.torch
         lg = t.zeros(S * self.sum_L2, dtype=t.float32, device=self.device) if logits else None
         sp = t.zeros(sum(L * (L + 1) for L in self.Ls) * self.chi, dtype=t.float64, device=self.device) if spectra else None
-        ri = t.zeros(sum(self.Ls) * 6, dtype=t.float64, device=self.device) if rowinfo else None
+        ri = t.zeros(sum(self.Ls) * 14, dtype=t.float64, device=self.device) if rowinfo else None
         self._diag = (lg, sp, ri)
         z = ctypes.c_void_p(0)
         _check(self.lib.tnmc_set_diagnostics(self.h, _ptr(lg) if lg is not None else z,

@@ -11,7 +11,7 @@
 
 namespace tnmc {
 cudaError_t launch_ingest(const Layout &lay, const float *J, cudaStream_t st);
-cudaError_t launch_env_build(const Layout &lay, int prec, int CH, cudaStream_t st);
+cudaError_t launch_env_build(const Layout &lay, int mode, int CH, cudaStream_t st);
 cudaError_t launch_log_z(const Layout &lay, int prec, double *logz, cudaStream_t st);
 cudaError_t launch_init_state(const Layout &lay, uint64_t seed, uint8_t *spins, cudaStream_t st);
 cudaError_t launch_mh(const Layout &lay, int S, uint64_t seed, uint64_t base, const uint8_t *ps,
@@ -21,7 +21,7 @@ cudaError_t launch_propose(const Layout &lay, int prec, int CH, int S, uint64_t 
                            uint64_t base, uint8_t *spins, double *lq, double *E, cudaStream_t st);
 cudaError_t launch_score(const Layout &lay, int prec, int CH, int S, const uint8_t *spins,
                          double *lq, double *E, cudaStream_t st);
-int64_t env_slot_bytes(int prec, int CH, int L_max);
+int64_t env_slot_bytes(int mode, int CH, int L_max, int chi);
 int64_t sampler_smem_bytes(int prec, int CH, int L_max);
 }  // namespace tnmc
 
@@ -55,16 +55,22 @@ tnmc_status check_cfg(const tnmc_config *cfg) {
   if (cfg->max_samples < 1 || cfg->max_samples > (1 << 24)) return TNMC_ERR_ARG;
   if (!std::isfinite(cfg->cutoff) || cfg->cutoff >= 1.0) return TNMC_ERR_ARG;
   if (cfg->prec == TNMC_TF32 || cfg->prec == TNMC_BF16) return TNMC_ERR_UNSUPPORTED;
-  if (cfg->prec != TNMC_FP64 && cfg->prec != TNMC_FP32) return TNMC_ERR_ARG;
+  if (cfg->prec != TNMC_FP64 && cfg->prec != TNMC_FP32 && cfg->prec != TNMC_MIXED) return TNMC_ERR_ARG;
   for (int n = 0; n < cfg->n_real; ++n)
     if (cfg->L[n] < 1 || cfg->L[n] > kMaxL) return TNMC_ERR_ARG;
   return TNMC_OK;
 }
 
+// 0: float64 build + float64 cache; 1: float32 build + cache; 2: float64 build, float32 cache
+int env_mode(int prec) { return prec == TNMC_FP64 ? 0 : (prec == TNMC_FP32 ? 1 : 2); }
+// type of the cache and of the sampler: 0 = float64, 1 = float32
+int cache_code(int prec) { return prec == TNMC_FP64 ? 0 : 1; }
+double default_cutoff(int prec) { return prec == TNMC_FP32 ? 1e-6 : 1e-12; }
+
 Plan make_plan(const tnmc_config *cfg) {
   Plan p;
   p.CH = pick_ch(cfg->chi);
-  const int64_t esz = cfg->prec == TNMC_FP64 ? 8 : 4;
+  const int64_t esz = cache_code(cfg->prec) == 0 ? 8 : 4;
   for (int n = 0; n < cfg->n_real; ++n) {
     const int64_t L = cfg->L[n];
     p.sum_L2 += L * L;
@@ -85,7 +91,7 @@ Plan make_plan(const tnmc_config *cfg) {
   p.off_bonds = take(p.sum_bonds * 8);
   p.off_lam = take(p.sum_L * 8);
   p.env_slots = std::min(cfg->n_real, kEnvSlots);
-  p.env_slot = env_slot_bytes(cfg->prec == TNMC_FP64 ? 0 : 1, p.CH, p.L_max);
+  p.env_slot = env_slot_bytes(env_mode(cfg->prec), p.CH, p.L_max, cfg->chi);
   p.env_bytes = p.env_slot * p.env_slots;
   p.off_env = take(p.env_bytes);
   p.samp_bytes = int64_t(cfg->max_samples) * p.sum_L * p.CH * esz;
@@ -103,7 +109,8 @@ struct tnmc_handle {
   tnmc_config cfg;
   Plan plan;
   Layout lay;
-  int prec_code;   // 0 = float64 kernels, 1 = float32 kernels
+  int env_code;    // env_mode()
+  int prec_code;   // cache_code(): sampler / log Z kernels on float64 (0) or float32 (1)
   cudaStream_t stream;
   bool built = false;
 };
@@ -158,7 +165,8 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
   h->cfg = *cfg;
   h->cfg.L = h->L.data();
   h->plan = p;
-  h->prec_code = cfg->prec == TNMC_FP64 ? 0 : 1;
+  h->env_code = env_mode(cfg->prec);
+  h->prec_code = cache_code(cfg->prec);
   h->stream = as_stream(cuda_stream);
   unsigned char *ws = static_cast<unsigned char *>(d_ws);
 
@@ -188,7 +196,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
   lay.L_max = p.L_max;
   lay.max_samples = cfg->max_samples;
   lay.beta = cfg->beta;
-  lay.cutoff = cfg->cutoff > 0 ? cfg->cutoff : (cfg->prec == TNMC_FP64 ? 1e-12 : 1e-6);
+  lay.cutoff = cfg->cutoff > 0 ? cfg->cutoff : default_cutoff(cfg->prec);
   lay.jr = reinterpret_cast<float *>(ws + p.off_jr);
   lay.jd = reinterpret_cast<float *>(ws + p.off_jd);
   lay.cache = ws + p.off_cache;
@@ -236,7 +244,7 @@ tnmc_status tnmc_build_envs(tnmc_handle *h, const float *d_J) {
   if (e == cudaSuccess && h->lay.dbg_spectra)
     e = cudaMemsetAsync(h->lay.dbg_spectra, 0,
                         size_t(h->plan.sum_bonds) * h->cfg.chi * sizeof(double), h->stream);
-  if (e == cudaSuccess) e = launch_env_build(h->lay, h->prec_code, h->plan.CH, h->stream);
+  if (e == cudaSuccess) e = launch_env_build(h->lay, h->env_code, h->plan.CH, h->stream);
   if (e != cudaSuccess) return TNMC_ERR_CUDA;
   h->built = true;
   return TNMC_OK;

@@ -29,32 +29,40 @@ namespace tnmc {
 namespace {
 
 constexpr int ENV_THREADS = 512;
-constexpr int JACOBI_MAX_SWEEPS = 40;
+constexpr int JACOBI_MAX_SWEEPS = 30;
 
-template <typename T, int CH>
+template <typename TC, typename TS, int CH>
 struct EnvPlan {
-  static constexpr int LDA = 2 * CH;                 // rows of the column-major A / Q panels
-  static constexpr int64_t CH2 = int64_t(CH) * CH;
-  // phase A (units of T)
-  static constexpr int64_t oCp = 0;                  // CH x CH, row-major (ld CH)
-  static constexpr int64_t oR = CH2;                 // 2 x (CH x CH), row-major (ld CH)
-  static constexpr int64_t oA = 3 * CH2;             // 2 x (2CH x CH), column-major (ld 2CH)
-  static constexpr int64_t oQf = 7 * CH2;            // 2 x (2CH x CH), column-major (ld 2CH)
-  // phase B (aliases phase A)
-  static constexpr int64_t oQc = 0;                  // 2CH x 2CH, column-major (ld 2CH); later V^T
+  static constexpr int LDA = 2 * CH;                 // rows of the column-major QR panels
   static constexpr int LDT = 2 * CH;                 // row length of Theta | U^T
-  static constexpr int64_t oTh = 4 * CH2;            // 2CH x 2CH, row-major (ld LDT)
-  static constexpr int64_t oUS = 8 * CH2;            // 2 x (CH x CH), row-major (ld CH)
-  static constexpr int64_t oTau = 11 * CH2;          // 2 x CH
+  static constexpr int64_t CH2 = int64_t(CH) * CH;
+  // phase A (units of TC)
+  static constexpr int64_t oR = 0;                   // 2 x (CH x CH), row-major (ld CH)
+  static constexpr int64_t oA = 2 * CH2;             // 2 x (2CH x CH), column-major (ld 2CH); Q in place
+  // phase B (aliases phase A; Theta must not alias R while the last site's GEMM reads R)
+  static constexpr int64_t oUS = 0;                  // 2 x (CH x CH), row-major (ld CH)
+  static constexpr int64_t oTh = 2 * CH2;            // 2CH x 2CH, row-major (ld LDT)
+  static constexpr int64_t oTau = 6 * CH2;           // 2 x CH
   static constexpr int64_t oSn = oTau + 2 * CH;      // 2CH singular values
   static constexpr int64_t nT = oSn + 2 * CH;
-  static constexpr int64_t bytes = nT * int64_t(sizeof(T));
-  static constexpr bool in_smem = bytes <= 200 * 1024;
-  // global scratch per slot: Q of every site + per-site dims (+ the arena when not in smem)
-  static __host__ __device__ int64_t q_bytes(int L_max) { return align256(int64_t(L_max) * LDA * LDA * sizeof(T)); }
-  static __host__ __device__ int64_t info_bytes(int L_max) { return align256(int64_t(L_max) * sizeof(int4)); }
-  static __host__ __device__ int64_t slot_bytes(int L_max) {
-    return q_bytes(L_max) + info_bytes(L_max) + (in_smem ? 0 : align256(bytes));
+  static constexpr int64_t bytes = nT * int64_t(sizeof(TC));
+  static constexpr bool in_smem = bytes <= 220 * 1024;
+  static constexpr bool split_carry = sizeof(TC) != sizeof(TS);
+  // global scratch per slot: Q of every site, per-site dims, the float64 carry
+  // of the previous row when the cache is stored narrower, and the work arena
+  // when it does not fit in shared memory
+  static __host__ __device__ int64_t q_bytes(int L_max) {
+    return align256(int64_t(L_max) * LDA * LDA * sizeof(TC));
+  }
+  static __host__ __device__ int64_t info_bytes(int L_max) {
+    return align256(int64_t(L_max) * sizeof(int4));
+  }
+  static __host__ __device__ int64_t carry_bytes(int L_max, int chi) {
+    return split_carry ? align256(int64_t(2) * L_max * chi * chi * sizeof(TC)) : 0;
+  }
+  static __host__ __device__ int64_t slot_bytes(int L_max, int chi) {
+    return q_bytes(L_max) + info_bytes(L_max) + carry_bytes(L_max, chi) +
+           (in_smem ? 0 : align256(bytes));
   }
 };
 
@@ -117,26 +125,32 @@ __device__ void householder_qr(T *A, int m, int n, T *tau, int half, int ht) {
   }
 }
 
-// Explicit Q (m x kq, column-major, ld LDA) from the reflectors left in A.
+// Explicit Q (m x kq, column-major, ld LDA) formed in place of the reflectors
+// left in A (LAPACK's org2r order: last reflector first; column j becomes
+// H_j e_j once the columns to its right are final).
 template <typename T, int LDA>
-__device__ void form_q(const T *A, const T *tau, T *Q, int m, int kq, int half, int ht) {
+__device__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int ht) {
   const int hw = ht >> 5, lane = ht & 31;
-  for (int idx = ht; idx < m * kq; idx += 256) {
-    const int i = idx % m, l = idx / m;
-    Q[int64_t(l) * LDA + i] = (i == l) ? T(1) : T(0);
-  }
-  half_barrier(half);
   for (int j = kq - 1; j >= 0; --j) {
     const T tj = tau[j];
     if (tj != T(0)) {
       const T *v = A + int64_t(j) * LDA;
-      for (int l = j + hw; l < kq; l += 8) {
-        T *ql = Q + int64_t(l) * LDA;
+      for (int l = j + 1 + hw; l < kq; l += 8) {
+        T *ql = A + int64_t(l) * LDA;
         T w = lane == 0 ? ql[j] : T(0);
         for (int i = j + 1 + lane; i < m; i += 32) w += v[i] * ql[i];
         w = warp_sum(w) * tj;
         if (lane == 0) ql[j] -= w;
         for (int i = j + 1 + lane; i < m; i += 32) ql[i] -= w * v[i];
+      }
+    }
+    half_barrier(half);
+    if (hw == 0) {
+      T *qj = A + int64_t(j) * LDA;
+      for (int i = lane; i < m; i += 32) {
+        if (i < j) qj[i] = T(0);
+        else if (i == j) qj[i] = T(1) - tj;
+        else qj[i] *= -tj;
       }
     }
     half_barrier(half);
@@ -149,104 +163,191 @@ __device__ __forceinline__ int seat_player(int seat, int k, int P) {
   return seat == 0 ? 0 : 1 + (seat - 1 + k) % (P - 1);
 }
 
+// Jacobi rotation (c, s, t = s / c) that orthogonalises two rows with squared
+// norms alpha, beta and inner product gamma. The angle only needs float32
+// accuracy (an inexact angle leaves a small residual for the next sweep), so
+// zeta and t are formed in float32; what must hold to working precision is
+// c^2 + s^2 = 1, or the rotation would not be orthogonal. For float64 the
+// float32 pair (c0, s0) is therefore rescaled by the series
+// 1 / sqrt(n) = 1 - d/2 + 3 d^2 / 8 (d = n - 1, |d| ~ 1e-7), exact to ~1e-21.
+// This keeps the float64 square roots and divisions (each a long sequence on
+// the float64 pipe) off the critical path of every Jacobi round.
+template <typename T>
+__device__ __forceinline__ void rotation_params(T al, T be, T ga, T &cs, T &sn, T &t);
+template <>
+__device__ __forceinline__ void rotation_params<float>(float al, float be, float ga, float &cs,
+                                                       float &sn, float &t) {
+  const float zeta = (be - al) / (2.f * ga);
+  const float az = fabsf(zeta);
+  t = az > 1e15f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(1.f + zeta * zeta));
+  if (zeta == 0.f) t = 1.f;
+  cs = rsqrtf(1.f + t * t);
+  sn = cs * t;
+}
+template <>
+__device__ __forceinline__ void rotation_params<double>(double al, double be, double ga, double &cs,
+                                                        double &sn, double &t) {
+  // zeta = (beta - alpha) / (2 gamma), scale-free, in float32: bring both
+  // operands into float range by the exponent of the larger one
+  const double num = be - al, den = 2.0 * ga;
+  const double big = fmax(fabs(num), fabs(den));
+  const int ex = ilogb(big);
+  const float fn = (float)scalbn(num, -ex), fd = (float)scalbn(den, -ex);
+  const float zeta = fn / fd;
+  const float az = fabsf(zeta);
+  float tf = az > 1e15f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(1.f + zeta * zeta));
+  if (fn == 0.f) tf = 1.f;
+  const float c0 = rsqrtf(1.f + tf * tf);
+  const double c = c0, s = (double)(c0 * tf);
+  const double d = fma(c, c, s * s) - 1.0;
+  const double r = fma(d, fma(0.375, d, -0.5), 1.0);
+  cs = c * r;
+  sn = s * r;
+  t = tf;   // s / c to float32 accuracy: only the cached norms use it
+}
+
 // One-sided (Hestenes) Jacobi on the rows of the nr x nc row-major matrix B
 // (ld ldb) by one half of the CTA: rotate row pairs until all rows are
 // mutually orthogonal to within tol. Afterwards row i = s_i v_i^T with s_i
 // a singular value and v_i the right singular vector. The rotations are also
 // applied to the nu extra columns that follow (an identity block on entry),
 // which then hold U^T, so that U S V^T reproduces B to rounding even though
-// the rows are only orthogonal to tol. Rotation: for rows a,
-// b with alpha = |a|^2, beta = |b|^2, gamma = a.b, zeta = (beta - alpha) / (2 gamma),
+// the rows are only orthogonal to tol. Rotation: for rows a, b with
+// alpha = |a|^2, beta = |b|^2, gamma = a.b, zeta = (beta - alpha) / (2 gamma),
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t:
-// a <- c a - s b, b <- s a + c b (Golub & Van Loan, Sec. 8.6.3).
-template <typename T, int CH>
-__device__ void jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int ht,
-                            volatile int *lastrot) {
-  constexpr int PAIRS = CH / 2 > 0 ? CH / 2 : 1;
-  constexpr int TPP = (256 / PAIRS) < 32 ? (256 / PAIRS) : 32;
-  if (nr <= 1) return;  // uniform over the half
+// a <- c a - s b, b <- s a + c b, and then alpha <- alpha - t gamma,
+// beta <- beta + t gamma (Golub & Van Loan, Sec. 8.6.3; de Rijk's cached
+// norms, refreshed in the first round of every sweep).
+// Only the warps that own a pair this round execute arithmetic: with float64
+// on B300 every idle warp's instruction costs the whole SM issue slots.
+template <typename T, int TPP>
+__device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int ht,
+                           volatile int *lastrot, T *nrm2, const int *perm) {
+  if (nr <= 1) return 0;  // uniform over the half
   const int P = nr + (nr & 1);
-  const int gi = ht / TPP, gl = ht % TPP;
-  const T tol = T(2) * Num<T>::eps() * Num<T>::sqrt_(T(nc > 4 ? nc : 4));
+  const int npairs = P / 2;
+  // the second half's active pairs start on the third scheduler partition, so
+  // both halves' float64 work spreads over all four partitions
+  const int vt = half ? ((ht + 192) & 255) : ht;
+  const int gi = vt / TPP, gl = vt % TPP;
+  const bool warp_active = (vt & ~31) < npairs * TPP;
+  // The computed cosine of a pair carries a rounding error ~ sqrt(nc) eps, so
+  // a tolerance at that floor never converges; 8 sqrt(nc) eps stops at the
+  // rounding level. Rotations whose tangent is below eps change nothing.
+  // float32 rounds are cheap, so float32 stops at 2 sqrt(nc) eps (more sweeps,
+  // rows orthogonal closer to the rounding floor); float64 at 8 sqrt(nc) eps
+  const T tf = sizeof(T) == 4 ? T(4) : T(64);
+  const T tol2 = tf * Num<T>::eps() * Num<T>::eps() * T(nc > 4 ? nc : 4);
+  for (int i = ht; i < nr; i += 256) {
+    T s2 = 0;
+    for (int x = 0; x < nc; ++x) { const T v = B[int64_t(i) * ldb + x]; s2 += v * v; }
+    nrm2[i] = s2;
+  }
+  half_barrier(half);
   for (int sweep = 0; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
     for (int k = 0; k < P - 1; ++k) {
-      int i = -1, j = -1;
-      if (gi < P / 2) {
-        i = seat_player(gi, k, P);
-        j = seat_player(P - 1 - gi, k, P);
-        if (i >= nr || j >= nr) i = j = -1;
-      }
-      T al = 0, be = 0, ga = 0;
-      if (i >= 0) {
-        const T *a = B + int64_t(i) * ldb, *b = B + int64_t(j) * ldb;
-        for (int x = gl; x < nc; x += TPP) {
-          const T av = a[x], bv = b[x];
-          al += av * av; be += bv * bv; ga += av * bv;
+      if (warp_active) {
+        int i = -1, j = -1;
+        if (gi < npairs) {
+          i = seat_player(gi, k, P);
+          j = seat_player(P - 1 - gi, k, P);
+          if (i >= nr || j >= nr) i = j = -1;
+          else { i = perm[i]; j = perm[j]; }
         }
-      }
-      al = group_sum<T, TPP>(al);
-      be = group_sum<T, TPP>(be);
-      ga = group_sum<T, TPP>(ga);
-      if (i >= 0 && ga != T(0) && fabs(ga) > tol * Num<T>::sqrt_(al * be)) {
-        const T zeta = (be - al) / (T(2) * ga);
-        const T az = fabs(zeta);
-        T t;
-        if (az > T(1) / Num<T>::eps()) t = T(0.5) / zeta;
-        else t = (zeta >= T(0) ? T(1) : T(-1)) / (az + Num<T>::sqrt_(T(1) + zeta * zeta));
-        const T cs = T(1) / Num<T>::sqrt_(T(1) + t * t), sn = cs * t;
-        T *a = B + int64_t(i) * ldb, *b = B + int64_t(j) * ldb;
-        for (int x = gl; x < nc + nu; x += TPP) {
-          const T av = a[x], bv = b[x];
-          a[x] = cs * av - sn * bv;
-          b[x] = sn * av + cs * bv;
+        const bool full = (k == 0);
+        T al = 0, be = 0, ga = 0;
+        if (i >= 0) {
+          const T *a = B + int64_t(i) * ldb, *b = B + int64_t(j) * ldb;
+          if (full) {
+            for (int x = gl; x < nc; x += TPP) {
+              const T av = a[x], bv = b[x];
+              al += av * av; be += bv * bv; ga += av * bv;
+            }
+          } else {
+            for (int x = gl; x < nc; x += TPP) ga += a[x] * b[x];
+          }
         }
-        if (gl == 0) *lastrot = sweep;
+        ga = group_sum<T, TPP>(ga);
+        if (full) {
+          al = group_sum<T, TPP>(al);
+          be = group_sum<T, TPP>(be);
+        } else if (i >= 0) {
+          al = nrm2[i];
+          be = nrm2[j];
+        }
+        __syncwarp();
+        if (i >= 0) {
+          // convergence test without a square root: gamma^2 > tol^2 alpha beta
+          bool rot = ga != T(0) && ga * ga > tol2 * (al * be);
+          T cs = 1, sn = 0, t = 0;
+          if (rot) rotation_params<T>(al, be, ga, cs, sn, t);
+          rot = rot && fabs(t) > Num<T>::eps();
+          if (rot) {
+            T *a = B + int64_t(i) * ldb, *b = B + int64_t(j) * ldb;
+            for (int x = gl; x < nc + nu; x += TPP) {
+              const T av = a[x], bv = b[x];
+              a[x] = cs * av - sn * bv;
+              b[x] = sn * av + cs * bv;
+            }
+            if (gl == 0) { nrm2[i] = al - t * ga; nrm2[j] = be + t * ga; *lastrot = sweep; }
+          } else if (full && gl == 0) {
+            nrm2[i] = al; nrm2[j] = be;
+          }
+        }
       }
       half_barrier(half);
     }
-    if (*lastrot < sweep) break;  // no rotation in this sweep (all threads agree)
+    if (*lastrot < sweep) return sweep + 1;  // no rotation in this sweep (all threads agree)
   }
+  return JACOBI_MAX_SWEEPS;
 }
 
-template <typename T>
+// Non-negative floating-point values order like their bit patterns.
+__device__ __forceinline__ long long order_key(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ long long order_key(float x) { return (long long)__float_as_int(x); }
+
 __device__ __forceinline__ double log_cosh(double x) {
   const double ax = fabs(x);
   return ax + log1p(exp(-2.0 * ax)) - 0.6931471805599453;
 }
 
-template <typename T, int CH>
+// TC: arithmetic of the build (and the carry between rows); TS: cache storage.
+template <typename TC, typename TS, int CH>
 __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
-  using P = EnvPlan<T, CH>;
-  constexpr int LDA = P::LDA;
+  using P = EnvPlan<TC, TS, CH>;
+  constexpr int LDA = P::LDA, LDT = P::LDT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh_red[ENV_THREADS / 32];
-  __shared__ double sh_lam;
-  __shared__ int sh_n, sh_kap0, sh_kap1, sh_newE, sh_newO, sh_ntr, sh_dmax;
-  __shared__ double sh_dsum;
+  __shared__ double sh_lam, sh_gap, sh_disc, sh_dsum, sh_flops;
+  __shared__ int sh_n, sh_kap0, sh_kap1, sh_newE, sh_newO, sh_ntr, sh_dmax, sh_sweeps, sh_svds;
   __shared__ int sh_lastrot[2];
-  __shared__ double sh_gap, sh_disc;
+  __shared__ int sh_keep[2 * CH];   // per candidate row: (sector << 16 | position) or -1
+  __shared__ int sh_src[2 * CH];    // Jacobi row order, then kept bond index -> candidate row
+  __shared__ long long sh_key[2 * CH];   // ordering keys of the singular values
+  __shared__ TC Bnrm[2 * CH];        // squared row norms cached by the Jacobi sweeps
+  __shared__ TC sh_tv, sh_th, sh_smax;
+  __shared__ long long sh_clk[5];    // cycles per phase of the current row (diagnostics)
+  long long t_mark = 0;
 
   const int tid = threadIdx.x, half = tid >> 8, ht = tid & 255;
   const int lane = tid & 31, warp = tid >> 5;
   const int chi = lay.chi;
+  const int64_t chi2 = int64_t(chi) * chi;
   const double beta = lay.beta;
 
   unsigned char *slot = (unsigned char *)lay.env_scratch + int64_t(blockIdx.x) * lay.env_slot_bytes;
-  T *Qstore = (T *)slot;
+  TC *Qstore = (TC *)slot;
   int4 *info = (int4 *)(slot + P::q_bytes(lay.L_max));
-  T *W = P::in_smem ? (T *)smem_raw
-                    : (T *)(slot + P::q_bytes(lay.L_max) + P::info_bytes(lay.L_max));
-  T *Cp = W + P::oCp;
-  T *Rb = W + P::oR;
-  T *Ab = W + P::oA;
-  T *Qf = W + P::oQf;
-  T *Qc = W + P::oQc;
-  T *Th = W + P::oTh;
-  constexpr int LDT = P::LDT;
-  T *US = W + P::oUS;
-  T *tau = W + P::oTau;
-  T *sn = W + P::oSn;
-  T *cache = (T *)lay.cache;
+  TC *carry = (TC *)(slot + P::q_bytes(lay.L_max) + P::info_bytes(lay.L_max));
+  TC *W = P::in_smem ? (TC *)smem_raw
+                     : (TC *)(slot + P::q_bytes(lay.L_max) + P::info_bytes(lay.L_max) +
+                              P::carry_bytes(lay.L_max, chi));
+  TC *Rb = W + P::oR;
+  TC *Ab = W + P::oA;
+  TC *US = W + P::oUS;
+  TC *Th = W + P::oTh;
+  TC *tau = W + P::oTau;
+  TC *sn = W + P::oSn;
 
   for (;;) {
     if (tid == 0) sh_n = atomicAdd(lay.counter, 1);
@@ -259,21 +360,25 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
     const int L = ri.L;
     const float *jr = lay.jr + ri.site_off;
     const float *jd = lay.jd + ri.site_off;
-    T *cache_n = cache + ri.site_off * int64_t(chi) * chi;
+    TS *cache_n = (TS *)lay.cache + ri.site_off * chi2;
     int2 *bonds_n = lay.bonds + ri.bond_off;
     if (lay.flags[n] & FLAG_BAD_J) continue;  // uniform: read by all threads after the barrier
 
     if (tid == 0) sh_lam = 0.0;
     for (int r = L - 1; r >= 0; --r) {
       const bool trivial_prev = (r == L - 1);
-      const T *cprev = cache_n + int64_t(r + 1) * L * chi * chi;  // unused when trivial_prev
+      // the previous row in the build's own precision
+      const TC *cprev = P::split_carry ? carry + int64_t((r + 1) & 1) * L * chi2
+                                       : (const TC *)(cache_n + int64_t(r + 1) * L * chi2);
+      TC *ccur = P::split_carry ? carry + int64_t(r & 1) * L * chi2 : nullptr;
+      TS *dst_row = cache_n + int64_t(r) * L * chi2;
       const int2 *bprev = bonds_n + int64_t(r + 1) * (L + 1);
       // ---- row constants: sum log cosh(beta Jh) + sum log 2 cosh(beta Jv) (row r < L-1)
       {
         double acc = 0.0;
         for (int c = tid; c < L; c += ENV_THREADS) {
-          if (c < L - 1) acc += log_cosh<T>(beta * (double)jr[r * L + c]);
-          if (r < L - 1) acc += log_cosh<T>(beta * (double)jd[r * L + c]) + 0.6931471805599453;
+          if (c < L - 1) acc += log_cosh(beta * (double)jr[r * L + c]);
+          if (r < L - 1) acc += log_cosh(beta * (double)jd[r * L + c]) + 0.6931471805599453;
         }
         acc = warp_sum(acc);
         if (lane == 0) sh_red[warp] = acc;
@@ -284,9 +389,10 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           sh_lam += s;
           sh_kap0 = 1; sh_kap1 = 0;
           sh_gap = 1e300; sh_disc = 0.0; sh_ntr = 0; sh_dmax = 0; sh_dsum = 0.0;
+          sh_sweeps = 0; sh_svds = 0; sh_flops = 0.0;
+          for (int q = 0; q < 5; ++q) sh_clk[q] = 0;
+          Rb[0] = TC(1);  // R of the absent site -1: the 1 x 1 identity of the trivial left bond
         }
-        // R of the (absent) site -1: the 1 x 1 identity of the trivial left bond
-        if (tid == 0) Rb[0] = T(1);
         __syncthreads();
       }
 
@@ -295,51 +401,58 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         const int2 bc = trivial_prev ? make_int2(1, 0) : bprev[c];
         const int2 bn = trivial_prev ? make_int2(1, 0) : bprev[c + 1];
         const int Dc = bc.x + bc.y, Dn = bn.x + bn.y;
-        const T tv = (r < L - 1) ? Num<T>::tanh_(T(beta) * T(jd[r * L + c])) : T(0);
-        const T th = (c < L - 1) ? Num<T>::tanh_(T(beta) * T(jr[r * L + c])) : T(0);
-        // 1. Ct: previous-row site with its odd-parity blocks scaled by t_v
-        for (int e = tid; e < Dc * Dn; e += ENV_THREADS) {
-          const int a = e / Dn, b = e % Dn;
-          T v = trivial_prev ? T(1) : cprev[int64_t(c) * chi * chi + int64_t(a) * chi + b];
-          if ((a >= bc.x) != (b >= bn.x)) v *= tv;
-          Cp[a * CH + b] = v;
+        if (tid == 0) {
+          sh_tv = (r < L - 1) ? Num<TC>::tanh_(TC(beta) * TC(jd[r * L + c])) : TC(0);
+          sh_th = (c < L - 1) ? Num<TC>::tanh_(TC(beta) * TC(jr[r * L + c])) : TC(0);
         }
         __syncthreads();
-        // 2. Y_q = R_q x (rows of Ct in sector-q order), scattered into the QR panels
+        const TC tv = sh_tv, th = sh_th;
+        const TC *Cp = cprev + int64_t(c) * chi2;
+        if (tid == 0) t_mark = clock64();
+        // Y_q = R_q x Ct[rows in sector-q order], Ct = previous site with its
+        // odd-parity blocks scaled by t_v; scattered into the two QR panels
         const int k0 = sh_kap0, k1 = sh_kap1, m = k0 + k1;
         for (int e = tid; e < m * Dn; e += ENV_THREADS) {
           const int i = e / Dn, b = e % Dn;
           const int q = (i >= k0) ? 1 : 0;
           const int ip = q ? i - k0 : i;
-          const T *Rrow = Rb + q * P::CH2 + int64_t(ip) * CH;
-          T acc = 0;
-          if (q == 0) {
-            for (int a = 0; a < Dc; ++a) acc += Rrow[a] * Cp[a * CH + b];
+          const TC *Rrow = Rb + q * P::CH2 + int64_t(ip) * CH;
+          const int pb = (b >= bn.x) ? 1 : 0;
+          TC acc = 0;
+          if (trivial_prev) {
+            acc = Rrow[0];
           } else {
             for (int a2 = 0; a2 < Dc; ++a2) {
-              const int a = (a2 < bc.y) ? bc.x + a2 : a2 - bc.y;
-              acc += Rrow[a2] * Cp[a * CH + b];
+              const int a = q == 0 ? a2 : ((a2 < bc.y) ? bc.x + a2 : a2 - bc.y);
+              TC v = Cp[int64_t(a) * chi + b];
+              if (((a >= bc.x) ? 1 : 0) != pb) v *= tv;
+              acc += Rrow[a2] * v;
             }
           }
           if (c < L - 1) {
-            const int par = (b >= bn.x) ? 1 : 0;
-            const int pos0 = par ? b - bn.x : b;
-            const int pos1 = par ? b : bn.y + b;
-            Ab[par * (LDA * CH) + int64_t(pos0) * LDA + i] = acc;
-            Ab[(1 - par) * (LDA * CH) + int64_t(pos1) * LDA + i] = th * acc;
+            const int pos0 = pb ? b - bn.x : b;
+            const int pos1 = pb ? b : bn.y + b;
+            Ab[pb * (LDA * CH) + int64_t(pos0) * LDA + i] = acc;
+            Ab[(1 - pb) * (LDA * CH) + int64_t(pos1) * LDA + i] = th * acc;
           } else {
             Th[int64_t(i) * LDT] = acc;  // last site: one column (trivial right bond)
           }
         }
         if (tid == 0) info[c] = make_int4(k0, k1, 0, 0);
         __syncthreads();
+        if (tid == 0) { const long long t1 = clock64(); sh_clk[0] += t1 - t_mark; t_mark = t1; }
         if (c == L - 1) break;
-        // 3. QR of each parity sector of the new right bond (both are m x Dn)
-        T *Aq = Ab + half * (LDA * CH);
-        householder_qr<T, LDA>(Aq, m, Dn, tau + half * CH, half, ht);
+        // QR of each parity sector of the new right bond (both are m x Dn)
+        TC *Aq = Ab + half * (LDA * CH);
+        householder_qr<TC, LDA>(Aq, m, Dn, tau + half * CH, half, ht);
         __syncthreads();
         const int kq = min(m, Dn);
-        // 4. R = upper trapezoid; normalise both sectors together
+        if (tid == 0) {
+          const double mm = m, nn = kq;
+          sh_flops += 2.0 * (2.0 * (2.0 * mm * nn * nn - 2.0 * nn * nn * nn / 3.0))  // QR + Q, 2 sectors
+                      + 2.0 * mm * Dn * Dc;                                          // MPO x MPS product
+        }
+        // R = upper trapezoid; both sectors normalised together
         {
           double acc = 0.0;
           for (int e = tid; e < 2 * kq * Dn; e += ENV_THREADS) {
@@ -357,25 +470,28 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
             if (ok) sh_lam += log(nrm);
             else set_flag(lay.flags, n, FLAG_NUMERIC);
           }
-          const T inv = ok ? T(1.0 / nrm) : T(0);
+          const TC inv = ok ? TC(1.0 / nrm) : TC(0);
           for (int e = tid; e < 2 * kq * Dn; e += ENV_THREADS) {
             const int q = e / (kq * Dn), rem = e % (kq * Dn), i = rem / Dn, b = rem % Dn;
             Rb[q * P::CH2 + int64_t(i) * CH + b] =
-                (b >= i) ? Ab[q * (LDA * CH) + int64_t(b) * LDA + i] * inv : T(0);
+                (b >= i) ? Ab[q * (LDA * CH) + int64_t(b) * LDA + i] * inv : TC(0);
           }
         }
-        // 5. explicit Q of each sector
-        form_q<T, LDA>(Aq, tau + half * CH, Qf + half * (LDA * CH), m, kq, half, ht);
         __syncthreads();
-        // 6. store Q_c = [Q_0 | Q_1] (m x 2kq, column-major) for phase B
-        T *qs = Qstore + int64_t(c) * LDA * LDA;
+        // explicit Q of each sector, in place of its reflectors
+        form_q_inplace<TC, LDA>(Aq, tau + half * CH, m, kq, half, ht);
+        __syncthreads();
+        if (tid == 0) { const long long t1 = clock64(); sh_clk[1] += t1 - t_mark; t_mark = t1; }
+        // store Q_c = [Q_0 | Q_1] (m x 2kq, column-major) for phase B
+        TC *qs = Qstore + int64_t(c) * LDA * LDA;
         for (int e = tid; e < 2 * kq * m; e += ENV_THREADS) {
           const int col = e / m, i = e % m;
           const int q = col / kq, l = col % kq;
-          qs[int64_t(col) * LDA + i] = Qf[q * (LDA * CH) + int64_t(l) * LDA + i];
+          qs[int64_t(col) * LDA + i] = Ab[q * (LDA * CH) + int64_t(l) * LDA + i];
         }
         if (tid == 0) { info[c].z = kq; sh_kap0 = kq; sh_kap1 = kq; }
         __syncthreads();
+        if (tid == 0) { const long long t1 = clock64(); sh_clk[0] += t1 - t_mark; t_mark = t1; }
       }
 
       // ================= phase B: right-to-left truncating SVD sweep
@@ -384,21 +500,19 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         const int4 inf = info[c];
         const int k0 = inf.x, k1 = inf.y, m = k0 + k1;
         const int N = curE + curO;
+        TS *dst = dst_row + int64_t(c) * chi2;
+        TC *cdst = P::split_carry ? ccur + int64_t(c) * chi2 : nullptr;
+        if (tid == 0) t_mark = clock64();
         if (c < L - 1) {
+          // Theta = Q_c x blockdiag(US_0, US_1); Q_c streamed from the slot scratch
           const int kq = inf.z;
-          const T *qs = Qstore + int64_t(c) * LDA * LDA;
-          for (int e = tid; e < 2 * kq * m; e += ENV_THREADS) {
-            const int col = e / m, i = e % m;
-            Qc[int64_t(col) * LDA + i] = qs[int64_t(col) * LDA + i];
-          }
-          __syncthreads();
-          // Theta = Q_c x blockdiag(US_0, US_1)
+          const TC *qs = Qstore + int64_t(c) * LDA * LDA;
           for (int e = tid; e < m * N; e += ENV_THREADS) {
             const int i = e / N, j = e % N;
             const int q = (j >= curE) ? 1 : 0, jp = q ? j - curE : j;
-            const T *Qcol = Qc + int64_t(q * kq) * LDA + i;
-            const T *Ucol = US + q * P::CH2 + jp;
-            T acc = 0;
+            const TC *Qcol = qs + int64_t(q * kq) * LDA + i;
+            const TC *Ucol = US + q * P::CH2 + jp;
+            TC acc = 0;
             for (int p = 0; p < kq; ++p) acc += Qcol[int64_t(p) * LDA] * Ucol[p * CH];
             Th[int64_t(i) * LDT + j] = acc;
           }
@@ -415,11 +529,12 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           for (int w = 0; w < ENV_THREADS / 32; ++w) nrm2 += sh_red[w];
           const double nrm = sqrt(nrm2);
           const bool ok = nrm > 0.0 && isfinite(nrm);
-          const T inv = ok ? T(1.0 / nrm) : T(0);
-          T *dst = cache_n + int64_t(r) * L * chi * chi;
-          for (int e = tid; e < chi * chi; e += ENV_THREADS) {
+          const TC inv = ok ? TC(1.0 / nrm) : TC(0);
+          for (int e = tid; e < chi2; e += ENV_THREADS) {
             const int a = e / chi, b = e % chi;
-            dst[e] = (a == 0 && b < N) ? Th[b] * inv : T(0);
+            const TC v = (a == 0 && b < N) ? Th[b] * inv : TC(0);
+            dst[e] = TS(v);
+            if (P::split_carry) cdst[e] = v;
           }
           if (tid == 0) {
             if (ok) sh_lam += log(nrm);
@@ -429,53 +544,96 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
             if (L > 1) bonds_n[int64_t(r) * (L + 1) + 1] = make_int2(curE, curO);
             lay.lam[ri.row_off + r] = sh_lam;
             if (lay.dbg_rowinfo) {
-              double *ro = lay.dbg_rowinfo + (ri.row_off + r) * 6;
+              double *ro = lay.dbg_rowinfo + (ri.row_off + r) * 14;
               ro[0] = sh_lam + 0.34657359027997264 * L;  // log ||F_r||: parity form has norm 2^(-L/2)
               ro[1] = sh_gap; ro[2] = sh_disc; ro[3] = sh_ntr;
               ro[4] = sh_dmax; ro[5] = L > 1 ? sh_dsum / (L - 1) : 1.0;
+              ro[6] = sh_svds; ro[7] = sh_svds > 0 ? double(sh_sweeps) / sh_svds : 0.0;
+              for (int q = 0; q < 5; ++q) ro[8 + q] = double(sh_clk[q]);
+              ro[13] = sh_flops;
             }
           }
           __syncthreads();
           break;
         }
-        // identity block after Theta: the rotations accumulate U^T there
+        // the rotations also accumulate U^T in an identity block after Theta, so
+        // that U S V^T reproduces Theta to rounding
         for (int e = tid; e < m * CH; e += ENV_THREADS) {
           const int i = e / CH, p = e % CH;
           const int base = (i >= k0) ? k0 : 0;
-          Th[int64_t(i) * LDT + N + p] = (p == i - base) ? T(1) : T(0);
+          Th[int64_t(i) * LDT + N + p] = (p == i - base) ? TC(1) : TC(0);
         }
         if (tid == 0) { sh_lastrot[0] = -1; sh_lastrot[1] = -1; }
+        // rows in decreasing norm (de Rijk's ordering speeds up the sweeps)
+        for (int i = tid; i < m; i += ENV_THREADS) {
+          TC s2 = 0;
+          for (int j = 0; j < N; ++j) { const TC v = Th[int64_t(i) * LDT + j]; s2 += v * v; }
+          sh_key[i] = order_key(s2);
+        }
         __syncthreads();
-        // SVD of each row-parity block (one per half)
+        for (int i = tid; i < m; i += ENV_THREADS) {
+          const int base = (i >= k0) ? k0 : 0, end = (i >= k0) ? m : k0;
+          int rank = 0;
+          for (int j = base; j < end; ++j)
+            rank += (sh_key[j] > sh_key[i]) || (sh_key[j] == sh_key[i] && j < i);
+          sh_src[base + rank] = i - base;   // sector-local row at sorted position
+        }
+        __syncthreads();
+        if (tid == 0) { const long long t1 = clock64(); sh_clk[2] += t1 - t_mark; t_mark = t1; }
         {
           const int rows = half ? k1 : k0;
-          T *Bq = Th + int64_t(half ? k0 : 0) * LDT;
-          jacobi_rows<T, CH>(Bq, rows, N, rows, LDT, half, ht, &sh_lastrot[half]);
+          int nsw;
+          TC *Bq = Th + int64_t(half ? k0 : 0) * LDT;
+          nsw = jacobi_rows<TC, 8>(Bq, rows, N, rows, LDT, half, ht, &sh_lastrot[half],
+                                   Bnrm + (half ? CH : 0), sh_src + (half ? k0 : 0));
+          if (ht == 0 && nsw > 0) { atomicAdd(&sh_sweeps, nsw); atomicAdd(&sh_svds, 1); }
         }
         __syncthreads();
+        if (tid == 0) { const long long t1 = clock64(); sh_clk[3] += t1 - t_mark; t_mark = t1; }
         // singular values = row norms
         for (int i = tid; i < m; i += ENV_THREADS) {
-          T s2 = 0;
-          for (int j = 0; j < N; ++j) { const T v = Th[int64_t(i) * LDT + j]; s2 += v * v; }
-          sn[i] = Num<T>::sqrt_(s2);
+          TC s2 = 0;
+          for (int j = 0; j < N; ++j) { const TC v = Th[int64_t(i) * LDT + j]; s2 += v * v; }
+          const TC si = Num<TC>::sqrt_(s2);
+          sn[i] = si;
+          sh_key[i] = order_key(si);
         }
         __syncthreads();
-        // selection of the chi largest (ties: lower index first); new position in its sector
-        T smax = 0;
-        for (int i = 0; i < m; ++i) smax = sn[i] > smax ? sn[i] : smax;
-        const T thr = smax * T(lay.cutoff);
-        __shared__ int sh_keep[2 * 64 * 2];   // per candidate: new index in the bond, or -1
-        __shared__ int sh_src[64];            // kept bond index -> candidate row
+        if (warp == 0) {
+          long long km = 0;
+          for (int i = lane; i < m; i += 32) km = sh_key[i] > km ? sh_key[i] : km;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            const long long other = __shfl_xor_sync(0xffffffffu, km, o);
+            km = other > km ? other : km;
+          }
+          if (lane == 0) {
+            TC smx = 0;
+            for (int i = 0; i < m; ++i) if (sh_key[i] == km) { smx = sn[i]; break; }
+            sh_smax = smx;
+          }
+        }
+        __syncthreads();
+        // keep the chi largest above cutoff x largest (ties: lower index first)
+        const TC smax = sh_smax;
+        const TC thr = smax * TC(lay.cutoff);
+        const long long kthr = order_key(thr);
         for (int i = tid; i < m; i += ENV_THREADS) {
-          const T si = sn[i];
+          const long long ki = sh_key[i];
           int rank = 0, pos = 0;
           const int qi = (i >= k0) ? 1 : 0;
           for (int j = 0; j < m; ++j) {
-            const bool before = (sn[j] > si) || (sn[j] == si && j < i);
+            const long long kj = sh_key[j];
+            const bool before = (kj > ki) || (kj == ki && j < i);
             rank += before;
-            if (before && ((j >= k0) ? 1 : 0) == qi && sn[j] > thr) pos += 1;  // provisional
+            if (before && ((j >= k0) ? 1 : 0) == qi) pos += 1;
           }
-          sh_keep[i] = (rank < chi && si > thr) ? (qi << 16) | pos : -1;
+          const TC si = sn[i];
+          const bool keep = rank < chi && ki > kthr;
+          sh_keep[i] = keep ? (qi << 16) | pos : -1;
+          if (keep && lay.dbg_spectra)
+            lay.dbg_spectra[(ri.bond_off + int64_t(r) * (L + 1) + c) * chi + rank] =
+                (double)si / (double)smax;
         }
         __syncthreads();
         if (tid == 0) {
@@ -492,8 +650,6 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
               drop_max = s > drop_max ? s : drop_max;
             }
           }
-          // positions counted above include only candidates above threshold, which are
-          // exactly the kept ones ranked before i within its sector (kept set = top-K)
           sh_newE = ne; sh_newO = no;
           sh_dmax = max(sh_dmax, ne + no);
           sh_dsum += ne + no;
@@ -503,41 +659,38 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
             sh_ntr += 1;
           }
           if (tot > 0.0) { const double d = drop / tot; sh_disc = d > sh_disc ? d : sh_disc; }
-          if (smax > T(0) && isfinite((double)smax)) sh_lam += log((double)smax);
+          if (smax > TC(0) && isfinite((double)smax)) sh_lam += log((double)smax);
           else set_flag(lay.flags, n, FLAG_NUMERIC);
         }
         __syncthreads();
         const int ne = sh_newE, no = sh_newO, nk = ne + no;
-        // V^T rows in the new bond order (even kept rows, then odd), into the Qc region
-        T *Vt = Qc;
-        for (int e = tid; e < m * N; e += ENV_THREADS) {
-          const int i = e / N, j = e % N;
-          const int kp = sh_keep[i];
-          if (kp >= 0) {
-            const int q = kp >> 16, pos = kp & 0xffff;
-            const int row = q ? ne + pos : pos;
-            Vt[int64_t(row) * CH + j] = Th[int64_t(i) * LDT + j] / sn[i];
-            if (j == 0) sh_src[row] = i;
+        if (tid == 0) {
+          for (int q = 0; q < 2; ++q) {
+            const double rq = q ? k1 : k0;
+            const double a = rq > N ? rq : N, b = rq > N ? N : rq;
+            if (b > 0) sh_flops += 4.0 * a * a * b + 8.0 * a * b * b + 9.0 * b * b * b;
           }
+          if (c < L - 1) sh_flops += 2.0 * m * N * inf.z;
         }
-        if (lay.dbg_spectra && tid < m && sh_keep[tid] >= 0) {
-          int rank = 0;
-          for (int j = 0; j < m; ++j) rank += (sn[j] > sn[tid]) || (sn[j] == sn[tid] && j < tid);
-          lay.dbg_spectra[(ri.bond_off + int64_t(r) * (L + 1) + c) * chi + rank] =
-              (double)sn[tid] / (double)smax;
+        // a kept candidate's position within its sector counts the kept candidates of that
+        // sector ranked before it (the kept set is the top of the ranking, so all of them)
+        for (int i = tid; i < m; i += ENV_THREADS) {
+          const int kp = sh_keep[i];
+          if (kp >= 0) sh_src[(kp >> 16) ? ne + (kp & 0xffff) : (kp & 0xffff)] = i;
+          Bnrm[i] = kp >= 0 ? TC(1) / sn[i] : TC(0);   // reciprocal singular values
         }
         __syncthreads();
-        // cache row r, site c
-        {
-          T *dst = cache_n + (int64_t(r) * L + c) * chi * chi;
-          for (int e = tid; e < chi * chi; e += ENV_THREADS) {
-            const int a = e / chi, b = e % chi;
-            dst[e] = (a < nk && b < N) ? Vt[int64_t(a) * CH + b] : T(0);
-          }
+        // cache row r, site c: V^T rows in the new bond order (even kept rows, then odd)
+        for (int e = tid; e < chi2; e += ENV_THREADS) {
+          const int a = e / chi, b = e % chi;
+          TC v = TC(0);
+          if (a < nk && b < N) { const int i = sh_src[a]; v = Th[int64_t(i) * LDT + b] * Bnrm[i]; }
+          dst[e] = TS(v);
+          if (P::split_carry) cdst[e] = v;
         }
         // U S from the accumulated rotations, per sector, divided by the largest singular value
         {
-          const T inv = smax > T(0) ? T(1) / smax : T(0);
+          const TC inv = smax > TC(0) ? TC(1) / smax : TC(0);
           for (int e = tid; e < (k0 * ne + k1 * no); e += ENV_THREADS) {
             int q, p, k;
             if (e < k0 * ne) { q = 0; p = e / ne; k = e % ne; }
@@ -549,6 +702,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         if (tid == 0) bonds_n[int64_t(r) * (L + 1) + c + 1] = make_int2(curE, curO);
         curE = ne; curO = no;
         __syncthreads();
+        if (tid == 0) { const long long t1 = clock64(); sh_clk[4] += t1 - t_mark; t_mark = t1; }
       }
     }
   }
@@ -556,58 +710,54 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
 
 }  // namespace
 
-template <typename T, int CH>
-static int64_t env_slot_bytes_t(int L_max) { return EnvPlan<T, CH>::slot_bytes(L_max); }
-
-int64_t env_slot_bytes(int prec, int CH, int L_max) {
-  if (prec == 0) {
-    switch (CH) {
-      case 8: return env_slot_bytes_t<double, 8>(L_max);
-      case 16: return env_slot_bytes_t<double, 16>(L_max);
-      case 32: return env_slot_bytes_t<double, 32>(L_max);
-      case 64: return env_slot_bytes_t<double, 64>(L_max);
-    }
-  } else {
-    switch (CH) {
-      case 8: return env_slot_bytes_t<float, 8>(L_max);
-      case 16: return env_slot_bytes_t<float, 16>(L_max);
-      case 32: return env_slot_bytes_t<float, 32>(L_max);
-      case 64: return env_slot_bytes_t<float, 64>(L_max);
-    }
+// Kernel variants: mode 0 = float64 build and cache; 1 = float32 build and
+// cache; 2 = float64 build with a float32 cache (the float64 carry between
+// rows stays in the slot scratch).
+template <typename TC, typename TS>
+static int64_t env_slot_bytes_ts(int CH, int L_max, int chi) {
+  switch (CH) {
+    case 8: return EnvPlan<TC, TS, 8>::slot_bytes(L_max, chi);
+    case 16: return EnvPlan<TC, TS, 16>::slot_bytes(L_max, chi);
+    case 32: return EnvPlan<TC, TS, 32>::slot_bytes(L_max, chi);
+    case 64: return EnvPlan<TC, TS, 64>::slot_bytes(L_max, chi);
   }
   return -1;
 }
 
-template <typename T, int CH>
+int64_t env_slot_bytes(int mode, int CH, int L_max, int chi) {
+  if (mode == 0) return env_slot_bytes_ts<double, double>(CH, L_max, chi);
+  if (mode == 1) return env_slot_bytes_ts<float, float>(CH, L_max, chi);
+  return env_slot_bytes_ts<double, float>(CH, L_max, chi);
+}
+
+template <typename TC, typename TS, int CH>
 static cudaError_t launch_env_t(const Layout &lay, cudaStream_t st) {
-  using P = EnvPlan<T, CH>;
+  using P = EnvPlan<TC, TS, CH>;
   const int smem = P::in_smem ? int(P::bytes) : 0;
-  cudaError_t e = cudaFuncSetAttribute(env_build_kernel<T, CH>,
+  cudaError_t e = cudaFuncSetAttribute(env_build_kernel<TC, TS, CH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(lay.counter, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  env_build_kernel<T, CH><<<lay.env_slots, ENV_THREADS, smem, st>>>(lay);
+  env_build_kernel<TC, TS, CH><<<lay.env_slots, ENV_THREADS, smem, st>>>(lay);
   return cudaGetLastError();
 }
 
-cudaError_t launch_env_build(const Layout &lay, int prec, int CH, cudaStream_t st) {
-  if (prec == 0) {
-    switch (CH) {
-      case 8: return launch_env_t<double, 8>(lay, st);
-      case 16: return launch_env_t<double, 16>(lay, st);
-      case 32: return launch_env_t<double, 32>(lay, st);
-      case 64: return launch_env_t<double, 64>(lay, st);
-    }
-  } else {
-    switch (CH) {
-      case 8: return launch_env_t<float, 8>(lay, st);
-      case 16: return launch_env_t<float, 16>(lay, st);
-      case 32: return launch_env_t<float, 32>(lay, st);
-      case 64: return launch_env_t<float, 64>(lay, st);
-    }
+template <typename TC, typename TS>
+static cudaError_t launch_env_ts(const Layout &lay, int CH, cudaStream_t st) {
+  switch (CH) {
+    case 8: return launch_env_t<TC, TS, 8>(lay, st);
+    case 16: return launch_env_t<TC, TS, 16>(lay, st);
+    case 32: return launch_env_t<TC, TS, 32>(lay, st);
+    case 64: return launch_env_t<TC, TS, 64>(lay, st);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_env_build(const Layout &lay, int mode, int CH, cudaStream_t st) {
+  if (mode == 0) return launch_env_ts<double, double>(lay, CH, st);
+  if (mode == 1) return launch_env_ts<float, float>(lay, CH, st);
+  return launch_env_ts<double, float>(lay, CH, st);
 }
 
 }  // namespace tnmc

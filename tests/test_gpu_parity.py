@@ -64,7 +64,7 @@ def test_fp64_log_z_spectra_and_proposals(P, Ls, chi, beta, kind):
     lq = props.logq.cpu().numpy()
     E = props.E.cpu().numpy()
     sp = sp.cpu().numpy()
-    ri = ri.cpu().numpy().reshape(-1, 6)
+    ri = ri.cpu().numpy().reshape(-1, 14)
     bo = ro = 0
     total_bd = 0
     for n, (L, (Jh, Jv), rows) in enumerate(zip(Ls, reals, envs)):
@@ -147,9 +147,10 @@ def test_fp64_mh_chain_bit_exact(P):
     assert total_acc > 0
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
 @pytest.mark.parametrize("Ls,chi,beta,kind", [([10, 7], 8, 2.0, "pmj"), ([8, 6], 16, 2.0, "pmj"),
                                              ([12], 8, 1.0, "gauss"), ([10], 32, 2.0, "pmj")])
-def test_fp32_log_z_and_draw_audit(P, Ls, chi, beta, kind):
+def test_fp32_log_z_and_draw_audit(P, Ls, chi, beta, kind, prec):
     """float32 mode against the float64 oracle.
 
     |d log Z| / L^2 <= 1e-6 (cases whose cut gaps are wide); energies exact;
@@ -160,7 +161,7 @@ def test_fp32_log_z_and_draw_audit(P, Ls, chi, beta, kind):
     bound here is 1e-2, not the float64 1e-9.
     """
     S = 64
-    t, reals, lz, props, (lg, _, _), st, flags = _run(P, Ls, chi, beta, "fp32", kind, S, diag=True)
+    t, reals, lz, props, (lg, _, _), st, flags = _run(P, Ls, chi, beta, prec, kind, S, diag=True)
     assert st == 0
     envs = parity.oracle_envs(reals, beta, chi, t.cutoff)   # the same truncation rule
     spins = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
@@ -204,3 +205,34 @@ def test_argument_errors(P):
     t.build_envs(torch.from_numpy(parity.packed_J(reals)).cuda())
     with pytest.raises(P.TnmcError):
         t.propose(5, 1)                                       # S > max_samples
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_beta3_float64_truncation_matches_oracle(P, prec):
+    """beta = 3: the float64 build (plain and mixed) follows the oracle row by row.
+
+    Per-row log ||F_r|| and the bond spectra agree to 1e-9; the proposals come
+    from an essentially exact q at this size (IS weights constant to 1e-6 for
+    float64 sampling, 1e-2 for float32 sampling).
+    """
+    Ls, chi, beta, S = [24], 32, 3.0, 64
+    t, reals, lz, props, (lg, sp, ri), st, flags = _run(P, Ls, chi, beta, prec, "pmj", S, diag=True)
+    assert st == 0
+    (Jh, Jv), = reals
+    rows = bmps.build_envs(Jh, Jv, beta, chi, t.cutoff)
+    ri = ri.cpu().numpy().reshape(-1, 14)
+    L = Ls[0]
+    for r in range(L):
+        # oracle lambda_r is log ||F_r|| (its MPS has unit norm)
+        assert abs(ri[r, 0] - rows[r].log_scale) < 1e-9 * abs(rows[r].log_scale), r
+    assert abs(lz[0] - bmps.log_z(rows)) < 1e-9 * abs(lz[0])
+    sp = sp.cpu().numpy().reshape(L, L + 1, chi)
+    for r in range(0, L, 5):
+        for c in range(1, L):
+            o_s = rows[r].spectra[c - 1]
+            np.testing.assert_allclose(sp[r, c, :o_s.size], o_s, rtol=1e-6, atol=1e-13)
+    if prec == "fp64":
+        # float32 sampling contractions lose the conditionals at beta = 3 (cancellation in
+        # rho_s = |l M R|, see test_precision_model.py); float64 keeps them
+        w = -(props.logq.cpu().numpy()[0] + beta * props.E.cpu().numpy()[0])
+        assert w.std() < 1e-6

@@ -99,4 +99,9 @@ def config(name: str) -> Workload:
         return Workload("gauss_L128_chi8_beta2_n128", [128] * 128, 2.0, 8, 256, kind="gauss")
     if name == "L1024":      # 64 +-J realizations, L=1024, beta=3, chi=32, S=128
         return Workload("L1024_chi32_beta3_n64_S128", [1024] * 64, 3.0, 32, 128)
+    # small cases of the L=256 workload's kernels (same beta, chi), for profiler captures
+    if name == "L128x8":
+        return Workload("L128_chi64_beta3_n8_S256", [128] * 8, 3.0, 64, 256)
+    if name == "L40x1":
+        return Workload("L40_chi64_beta3_n1_S64", [40], 3.0, 64, 64)
     raise KeyError(name)
