@@ -187,6 +187,32 @@ tnmc_status tnmc_mh_step(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
 tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spectra,
                                  double *d_rowinfo);
 
+/* Proposals without caller-provided scratch (the paper has no counterpart).
+ * Same results and layouts as tnmc_propose, bit for bit, but the right
+ * environments of the chains (S x sum_n L_n x chi values, 8 bytes each in
+ * TNMC_FP64 mode, 4 otherwise, chi rounded up to 8/16/32/64) live in a
+ * fixed 32 MiB device array owned by the library instead of the workspace.
+ * It is for callers that cannot allocate device memory at the point of the
+ * call: code running under a memory pool that is already fully reserved,
+ * inside a region where the allocator must not be entered, or in a runtime
+ * that owns all allocations and hands this library only the buffers it asked
+ * for at setup. S may exceed the handle's max_samples as long as the scratch
+ * fits in the array; larger requests return TNMC_ERR_ARG (see
+ * tnmc_propose_static_limit). Nothing is allocated: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ * Every call shares the one array, and nothing in it needs to start at zero
+ * (each value read is written earlier in the same launch). Calls that overlap
+ * on the GPU -- two streams, or two handles at the same time -- race on the
+ * array and must be ordered by the caller. The first call on a device looks
+ * up the array's device address once (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.
+ * Errors: TNMC_ERR_ARG, TNMC_ERR_STATE, TNMC_ERR_CUDA. */
+tnmc_status tnmc_propose_static(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop_base,
+                                uint8_t *d_spins, double *d_logq, double *d_E);
+
+/* Bytes of the fixed device array used by tnmc_propose_static. */
+size_t tnmc_propose_static_limit(void);
+
 /* Copy the per-realization device flags (TNMC_FLAG_*) to h_flags [n_real],
  * after synchronising the stream; clears them when clear != 0.
  * Returns TNMC_OK, or TNMC_ERR_NUMERIC / TNMC_ERR_TIMEOUT if any flag of

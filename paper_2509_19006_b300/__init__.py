@@ -26,6 +26,7 @@ EXPORTED = [
     "tnmc_status_string", "tnmc_workspace_size", "tnmc_create", "tnmc_destroy",
     "tnmc_build_envs", "tnmc_log_z", "tnmc_propose", "tnmc_score", "tnmc_mh_init",
     "tnmc_mh_step", "tnmc_set_diagnostics", "tnmc_get_device_status", "tnmc_layout_info",
+    "tnmc_propose_static", "tnmc_propose_static_limit",
 ]
 
 
@@ -74,6 +75,8 @@ def load_library():
         "tnmc_mh_step": ([vp, i32, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "tnmc_set_diagnostics": ([vp, vp, vp, vp], i32),
         "tnmc_get_device_status": ([vp, vp, i32], i32),
+        "tnmc_propose_static": ([vp, i32, u64, u64, vp, vp, vp], i32),
+        "tnmc_propose_static_limit": ([], sz),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -208,6 +211,14 @@ class TNMC:
         out.S, out.prop_base = S, prop_base
         _check(self.lib.tnmc_propose(self.h, int(S), int(seed), int(prop_base), _ptr(out.spins),
                                      _ptr(out.logq), _ptr(out.E)), "tnmc_propose")
+        return out
+
+    def propose_static(self, S: int, seed: int, prop_base: int = 0, out: Optional[Proposals] = None) -> Proposals:
+        """tnmc_propose with the library's fixed scratch array (no workspace scratch needed)."""
+        out = out if out is not None else self.alloc_proposals(S, prop_base)
+        out.S, out.prop_base = S, prop_base
+        _check(self.lib.tnmc_propose_static(self.h, int(S), int(seed), int(prop_base), _ptr(out.spins),
+                                            _ptr(out.logq), _ptr(out.E)), "tnmc_propose_static")
         return out
 
     def score(self, spins, S: int):

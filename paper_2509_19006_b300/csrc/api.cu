@@ -22,6 +22,10 @@ cudaError_t launch_propose(const Layout &lay, int prec, int CH, int S, uint64_t 
 cudaError_t launch_score(const Layout &lay, int prec, int CH, int S, const uint8_t *spins,
                          double *lq, double *E, cudaStream_t st);
 int64_t env_slot_bytes(int mode, int CH, int L_max, int chi);
+cudaError_t launch_propose_static(const Layout &lay, int prec, int CH, int S, uint64_t seed,
+                                  uint64_t base, uint8_t *spins, double *lq, double *E,
+                                  int64_t sum_L, cudaStream_t st, bool *too_big);
+int64_t static_scratch_bytes();
 int64_t sampler_smem_bytes(int prec, int CH, int L_max);
 }  // namespace tnmc
 
@@ -267,6 +271,21 @@ tnmc_status tnmc_propose(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
              ? TNMC_OK
              : TNMC_ERR_CUDA;
 }
+
+tnmc_status tnmc_propose_static(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop_base,
+                                uint8_t *d_spins, double *d_logq, double *d_E) {
+  if (!h || !d_spins || !d_logq || !d_E) return TNMC_ERR_ARG;
+  if (S < 1) return TNMC_ERR_ARG;
+  if (!h->built) return TNMC_ERR_STATE;
+  bool too_big = false;
+  const cudaError_t e = launch_propose_static(h->lay, h->prec_code, h->plan.CH, S, seed, prop_base,
+                                              d_spins, d_logq, d_E, h->plan.sum_L, h->stream,
+                                              &too_big);
+  if (too_big) return TNMC_ERR_ARG;
+  return e == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
+}
+
+size_t tnmc_propose_static_limit(void) { return size_t(static_scratch_bytes()); }
 
 tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins, double *d_logq,
                        double *d_E) {

@@ -19,6 +19,8 @@
 // chains' vectors (shared memory, chain-minor).
 #include "common.cuh"
 
+#include <mutex>
+
 namespace tnmc {
 
 namespace {
@@ -391,6 +393,59 @@ cudaError_t launch_propose(const Layout &lay, int prec, int CH, int S, uint64_t 
 cudaError_t launch_score(const Layout &lay, int prec, int CH, int S, const uint8_t *spins,
                          double *lq, double *E, cudaStream_t st) {
   return launch_samp<true>(lay, prec, CH, S, 0, 0, spins, nullptr, lq, E, st);
+}
+
+// ---------------------------------------------------------------------------
+// Proposals without caller-provided scratch. The right environments live in a
+// fixed device array owned by this library instead of the workspace. Every
+// device that loads the library holds the array until the process exits.
+constexpr int64_t kStaticScratchBytes = int64_t(32) << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_propose_scratch[kStaticScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void *g_scratch_ptr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+}  // namespace
+
+int64_t static_scratch_bytes() { return kStaticScratchBytes; }
+
+// Address of the array on the current device. The array's name in host code is
+// only a host-side stand-in, so the device address is looked up once per
+// device (with that device current) and cached.
+static cudaError_t static_scratch_address(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_propose_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+// Same kernel as launch_propose; only the scratch pointer and its per-line
+// stride (S chains instead of max_samples) differ. Nothing in the scratch has
+// to start at zero: every element the kernel reads was written earlier in the
+// same launch.
+cudaError_t launch_propose_static(const Layout &lay, int prec, int CH, int S, uint64_t seed,
+                                  uint64_t base, uint8_t *spins, double *lq, double *E,
+                                  int64_t sum_L, cudaStream_t st, bool *too_big) {
+  const int64_t esz = prec == 0 ? 8 : 4;
+  *too_big = int64_t(S) * sum_L * CH * esz > kStaticScratchBytes;
+  if (*too_big) return cudaSuccess;
+  void *scratch = nullptr;
+  cudaError_t e = static_scratch_address(&scratch);
+  if (e != cudaSuccess) return e;
+  Layout l2 = lay;
+  l2.samp_scratch = scratch;
+  l2.max_samples = S;
+  return launch_samp<false>(l2, prec, CH, S, seed, base, nullptr, spins, lq, E, st);
 }
 
 int64_t sampler_smem_bytes(int prec, int CH, int L_max) {
