@@ -34,7 +34,7 @@ constexpr int JACOBI_MAX_SWEEPS = 30;
 template <typename TC, typename TS, int CH>
 struct EnvPlan {
   static constexpr int LDA = 2 * CH;                 // rows of the column-major QR panels
-  static constexpr int LDT = 2 * CH;                 // row length of Theta | U^T
+  static constexpr int LDT = 2 * CH + 1;             // row stride of Theta | U^T (odd: no bank conflicts between rows)
   static constexpr int64_t CH2 = int64_t(CH) * CH;
   // phase A (units of TC)
   static constexpr int64_t oR = 0;                   // 2 x (CH x CH), row-major (ld CH)
@@ -42,7 +42,7 @@ struct EnvPlan {
   // phase B (aliases phase A; Theta must not alias R while the last site's GEMM reads R)
   static constexpr int64_t oUS = 0;                  // 2 x (CH x CH), row-major (ld CH)
   static constexpr int64_t oTh = 2 * CH2;            // 2CH x 2CH, row-major (ld LDT)
-  static constexpr int64_t oTau = 6 * CH2;           // 2 x CH
+  static constexpr int64_t oTau = oTh + 2 * CH * LDT;  // 2 x CH
   static constexpr int64_t oSn = oTau + 2 * CH;      // 2CH singular values
   static constexpr int64_t nT = oSn + 2 * CH;
   static constexpr int64_t bytes = nT * int64_t(sizeof(TC));
@@ -184,26 +184,39 @@ __device__ __forceinline__ void rotation_params<float>(float al, float be, float
   cs = rsqrtf(1.f + t * t);
   sn = cs * t;
 }
+__device__ __forceinline__ double rcp_approx(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+__device__ __forceinline__ double rsqrt_approx(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
 template <>
 __device__ __forceinline__ void rotation_params<double>(double al, double be, double ga, double &cs,
                                                         double &sn, double &t) {
-  // zeta = (beta - alpha) / (2 gamma), scale-free, in float32: bring both
-  // operands into float range by the exponent of the larger one
-  const double num = be - al, den = 2.0 * ga;
-  const double big = fmax(fabs(num), fabs(den));
-  const int ex = ilogb(big);
-  const float fn = (float)scalbn(num, -ex), fd = (float)scalbn(den, -ex);
-  const float zeta = fn / fd;
-  const float az = fabsf(zeta);
-  float tf = az > 1e15f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(1.f + zeta * zeta));
-  if (fn == 0.f) tf = 1.f;
-  const float c0 = rsqrtf(1.f + tf * tf);
-  const double c = c0, s = (double)(c0 * tf);
-  const double d = fma(c, c, s * s) - 1.0;
+  // angle to ~float32 accuracy from the hardware's approximate float64
+  // reciprocal and reciprocal square root (no float64 division or sqrt)
+  const double num = be - al;
+  const double zeta = num * rcp_approx(2.0 * ga);
+  const double az = fabs(zeta);
+  double tt;
+  if (az > 1e15) tt = 0.5 * rcp_approx(zeta);
+  else {
+    const double q = fma(zeta, zeta, 1.0);
+    tt = copysign(rcp_approx(az + q * rsqrt_approx(q)), zeta);
+  }
+  if (num == 0.0) tt = 1.0;
+  const double c0 = rsqrt_approx(fma(tt, tt, 1.0));
+  const double s0 = c0 * tt;
+  // c^2 + s^2 = 1 to working precision: rescale by 1/sqrt(1+d) ~ 1 - d/2 + 3d^2/8
+  const double d = fma(c0, c0, fma(s0, s0, -1.0));
   const double r = fma(d, fma(0.375, d, -0.5), 1.0);
-  cs = c * r;
-  sn = s * r;
-  t = tf;   // s / c to float32 accuracy: only the cached norms use it
+  cs = c0 * r;
+  sn = s0 * r;
+  t = tt;
 }
 
 // One-sided (Hestenes) Jacobi on the rows of the nr x nc row-major matrix B
@@ -244,6 +257,15 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
     nrm2[i] = s2;
   }
   half_barrier(half);
+  // rows whose norm is below eps x the largest are rounding noise: rotating them
+  // only stirs noise (they never pass any cutoff), so they are left alone
+  T floor2 = 0;
+  if (warp_active) {
+    T mx = 0;
+    for (int i = 0; i < nr; ++i) mx = nrm2[i] > mx ? nrm2[i] : mx;
+    floor2 = sizeof(T) == 8 ? mx * Num<T>::eps() * Num<T>::eps() : T(0);
+  }
+  half_barrier(half);
   for (int sweep = 0; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
     for (int k = 0; k < P - 1; ++k) {
       if (warp_active) {
@@ -278,7 +300,7 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
         __syncwarp();
         if (i >= 0) {
           // convergence test without a square root: gamma^2 > tol^2 alpha beta
-          bool rot = ga != T(0) && ga * ga > tol2 * (al * be);
+          bool rot = ga != T(0) && ga * ga > tol2 * (al * be) && al > floor2 && be > floor2;
           T cs = 1, sn = 0, t = 0;
           if (rot) rotation_params<T>(al, be, ga, cs, sn, t);
           rot = rot && fabs(t) > Num<T>::eps();
@@ -584,7 +606,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           const int rows = half ? k1 : k0;
           int nsw;
           TC *Bq = Th + int64_t(half ? k0 : 0) * LDT;
-          nsw = jacobi_rows<TC, 8>(Bq, rows, N, rows, LDT, half, ht, &sh_lastrot[half],
+          nsw = jacobi_rows<TC, 4>(Bq, rows, N, rows, LDT, half, ht, &sh_lastrot[half],
                                    Bnrm + (half ? CH : 0), sh_src + (half ? k0 : 0));
           if (ht == 0 && nsw > 0) { atomicAdd(&sh_sweeps, nsw); atomicAdd(&sh_svds, 1); }
         }
