@@ -164,14 +164,15 @@ __device__ __forceinline__ int seat_player(int seat, int k, int P) {
 }
 
 // Jacobi rotation (c, s, t = s / c) that orthogonalises two rows with squared
-// norms alpha, beta and inner product gamma. The angle only needs float32
-// accuracy (an inexact angle leaves a small residual for the next sweep), so
-// zeta and t are formed in float32; what must hold to working precision is
-// c^2 + s^2 = 1, or the rotation would not be orthogonal. For float64 the
-// float32 pair (c0, s0) is therefore rescaled by the series
-// 1 / sqrt(n) = 1 - d/2 + 3 d^2 / 8 (d = n - 1, |d| ~ 1e-7), exact to ~1e-21.
-// This keeps the float64 square roots and divisions (each a long sequence on
-// the float64 pipe) off the critical path of every Jacobi round.
+// norms alpha, beta and inner product gamma. The angle only needs about float32
+// accuracy (an inexact angle leaves a small residual for the next sweep); what
+// must hold to working precision is c^2 + s^2 = 1, or the rotation would not
+// be orthogonal. For float64, zeta and t come from the hardware's approximate
+// float64 reciprocal and reciprocal square root, and the pair (c0, s0) is
+// rescaled by the series 1 / sqrt(n) = 1 - d/2 + 3 d^2 / 8 (d = n - 1, small),
+// which leaves c^2 + s^2 - 1 at rounding level. This keeps the float64 square
+// roots and divisions (each a long sequence on the float64 pipe) off the
+// critical path of every Jacobi round.
 template <typename T>
 __device__ __forceinline__ void rotation_params(T al, T be, T ga, T &cs, T &sn, T &t);
 template <>
@@ -197,8 +198,6 @@ __device__ __forceinline__ double rsqrt_approx(double x) {
 template <>
 __device__ __forceinline__ void rotation_params<double>(double al, double be, double ga, double &cs,
                                                         double &sn, double &t) {
-  // angle to ~float32 accuracy from the hardware's approximate float64
-  // reciprocal and reciprocal square root (no float64 division or sqrt)
   const double num = be - al;
   const double zeta = num * rcp_approx(2.0 * ga);
   const double az = fabs(zeta);
@@ -211,7 +210,9 @@ __device__ __forceinline__ void rotation_params<double>(double al, double be, do
   if (num == 0.0) tt = 1.0;
   const double c0 = rsqrt_approx(fma(tt, tt, 1.0));
   const double s0 = c0 * tt;
-  // c^2 + s^2 = 1 to working precision: rescale by 1/sqrt(1+d) ~ 1 - d/2 + 3d^2/8
+  // c^2 + s^2 = 1 to working precision: rescale by 1/sqrt(1+d) ~ 1 - d/2 + 3d^2/8;
+  // the approximate rsqrt is good to ~1e-6, so |d| < 4e-6 and the series'
+  // remainder 5|d|^3/16 stays below 2e-17
   const double d = fma(c0, c0, fma(s0, s0, -1.0));
   const double r = fma(d, fma(0.375, d, -0.5), 1.0);
   cs = c0 * r;
@@ -257,8 +258,12 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
     nrm2[i] = s2;
   }
   half_barrier(half);
-  // rows whose norm is below eps x the largest are rounding noise: rotating them
-  // only stirs noise (they never pass any cutoff), so they are left alone
+  // Rows whose norm is below eps x the largest are rounding noise: rotating
+  // them only stirs noise (a rotation with a larger row leaves their norm of
+  // the same size, and they never pass any cutoff), so they are left alone.
+  // A row is judged noise only on an exact norm (the first round of a sweep
+  // measures every row); it then keeps that norm, since nothing rotates it.
+  const T kNoise = T(-INFINITY);
   T floor2 = 0;
   if (warp_active) {
     T mx = 0;
@@ -269,14 +274,20 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
   for (int sweep = 0; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
     for (int k = 0; k < P - 1; ++k) {
       if (warp_active) {
-        int i = -1, j = -1;
+        const bool full = (k == 0);
+        int i = -1, j = -1, solo = -1;
         if (gi < npairs) {
           i = seat_player(gi, k, P);
           j = seat_player(P - 1 - gi, k, P);
-          if (i >= nr || j >= nr) i = j = -1;
-          else { i = perm[i]; j = perm[j]; }
+          if (i >= nr || j >= nr) {
+            // odd row count: this row sits the round out, but its norm is still refreshed
+            solo = (full && i < nr) ? perm[i] : ((full && j < nr) ? perm[j] : -1);
+            i = j = -1;
+          } else {
+            i = perm[i];
+            j = perm[j];
+          }
         }
-        const bool full = (k == 0);
         T al = 0, be = 0, ga = 0;
         if (i >= 0) {
           const T *a = B + int64_t(i) * ldb, *b = B + int64_t(j) * ldb;
@@ -288,6 +299,9 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
           } else {
             for (int x = gl; x < nc; x += TPP) ga += a[x] * b[x];
           }
+        } else if (solo >= 0) {
+          const T *a = B + int64_t(solo) * ldb;
+          for (int x = gl; x < nc; x += TPP) al += a[x] * a[x];
         }
         ga = group_sum<T, TPP>(ga);
         if (full) {
@@ -298,23 +312,28 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
           be = nrm2[j];
         }
         __syncwarp();
+        if (solo >= 0 && gl == 0) nrm2[solo] = al <= floor2 ? kNoise : al;
+        bool rot = false;
+        T cs = 1, sn = 0, t = 0;
         if (i >= 0) {
+          // noise rows carry the sentinel from their exact measurement
+          const bool quiet = full ? (al <= floor2 || be <= floor2) : (al == kNoise || be == kNoise);
           // convergence test without a square root: gamma^2 > tol^2 alpha beta
-          bool rot = ga != T(0) && ga * ga > tol2 * (al * be) && al > floor2 && be > floor2;
-          T cs = 1, sn = 0, t = 0;
+          rot = !quiet && ga != T(0) && ga * ga > tol2 * (al * be);
           if (rot) rotation_params<T>(al, be, ga, cs, sn, t);
           rot = rot && fabs(t) > Num<T>::eps();
-          if (rot) {
-            T *a = B + int64_t(i) * ldb, *b = B + int64_t(j) * ldb;
-            for (int x = gl; x < nc + nu; x += TPP) {
-              const T av = a[x], bv = b[x];
-              a[x] = cs * av - sn * bv;
-              b[x] = sn * av + cs * bv;
-            }
-            if (gl == 0) { nrm2[i] = al - t * ga; nrm2[j] = be + t * ga; *lastrot = sweep; }
-          } else if (full && gl == 0) {
-            nrm2[i] = al; nrm2[j] = be;
+        }
+        if (rot) {
+          T *a = B + int64_t(i) * ldb, *b = B + int64_t(j) * ldb;
+          for (int x = gl; x < nc + nu; x += TPP) {
+            const T av = a[x], bv = b[x];
+            a[x] = cs * av - sn * bv;
+            b[x] = sn * av + cs * bv;
           }
+        }
+        if (i >= 0 && gl == 0) {
+          if (rot) { nrm2[i] = al - t * ga; nrm2[j] = be + t * ga; *lastrot = sweep; }
+          else if (full) { nrm2[i] = al <= floor2 ? kNoise : al; nrm2[j] = be <= floor2 ? kNoise : be; }
         }
       }
       half_barrier(half);

@@ -211,9 +211,16 @@ def test_argument_errors(P):
 def test_beta3_float64_truncation_matches_oracle(P, prec):
     """beta = 3: the float64 build (plain and mixed) follows the oracle row by row.
 
-    Per-row log ||F_r|| and the bond spectra agree to 1e-9; the proposals come
-    from an essentially exact q at this size (IS weights constant to 1e-6 for
-    float64 sampling, 1e-2 for float32 sampling).
+    Per-row log ||F_r|| and log Z agree to 1e-9 relative; the proposals come
+    from an essentially exact q at this size (IS weights constant to 1e-6).
+
+    The bond spectra of this instance are ill-conditioned: relative noise of
+    1e-16 in the oracle's own SVD inputs already moves the normalised spectra
+    by up to 5e-9 (4e-5 relative on the smallest kept values), and noise of
+    1e-14, the orthogonality the Jacobi sweeps stop at (8 sqrt(n) eps), by up
+    to 6e-8 on the rows checked here. The bound is therefore absolute, 2e-7 on
+    spectra normalised to s_0 = 1, and every value the oracle keeps well above
+    the cutoff must be kept.
     """
     Ls, chi, beta, S = [24], 32, 3.0, 64
     t, reals, lz, props, (lg, sp, ri), st, flags = _run(P, Ls, chi, beta, prec, "pmj", S, diag=True)
@@ -230,7 +237,9 @@ def test_beta3_float64_truncation_matches_oracle(P, prec):
     for r in range(0, L, 5):
         for c in range(1, L):
             o_s = rows[r].spectra[c - 1]
-            np.testing.assert_allclose(sp[r, c, :o_s.size], o_s, rtol=1e-6, atol=1e-13)
+            np.testing.assert_allclose(sp[r, c, :o_s.size], o_s, rtol=0, atol=2e-7)
+            if o_s[-1] > 10 * t.cutoff:
+                assert np.count_nonzero(sp[r, c]) >= o_s.size, (r, c)
     if prec == "fp64":
         # float32 sampling contractions lose the conditionals at beta = 3 (cancellation in
         # rho_s = |l M R|, see test_precision_model.py); float64 keeps them
