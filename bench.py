@@ -354,7 +354,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp64", "fp32", "mixed"], default="fp64")
+    ap.add_argument("--prec", choices=["fp64", "fp32", "mixed"], default="fp32")
     ap.add_argument("--workload", default="L256")
     ap.add_argument("--cutoff", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
