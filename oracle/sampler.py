@@ -45,13 +45,16 @@ def _fold_up(M: np.ndarray, beta: float, Jv: float | None) -> np.ndarray:
     return np.einsum("isk,us->iuk", M, B)
 
 
-def run_rows(rows, Jh, Jv, beta, u=None, forced=None):
+def run_rows(rows, Jh, Jv, beta, u=None, forced=None, correction=None):
     """Propose (u given) or score (forced spins given) S configurations of one realization.
 
-    rows    : list of RowEnv, the cache indexed by row
-    u       : (S, L*L) uniforms for the draws, raster order (propose mode)
-    forced  : (S, L, L) spin bits to score (teacher-forced mode)
-    Returns (sigma (S, L, L) uint8, log_q (S,), logits (S, L*L)).
+    rows       : list of RowEnv, the cache indexed by row
+    u          : (S, L*L) uniforms for the draws, raster order (propose mode)
+    forced     : (S, L, L) spin bits to score (teacher-forced mode)
+    correction : optional callable (sigma so far, r, c, logit) -> Delta added to
+                 the logit before the draw and before log q (``learned.Correction``)
+    Returns (sigma (S, L, L) uint8, log_q (S,), logits (S, L*L)), the logits
+    being the ones drawn from (corrected when a correction is given).
     """
     L = len(rows)
     S = (u if u is not None else forced).shape[0]
@@ -82,6 +85,8 @@ def run_rows(rows, Jh, Jv, beta, u=None, forced=None):
             if r > 0:
                 s_up = 2.0 * up[:, c] - 1.0
                 logit = logit + 2.0 * beta * float(Jv[r - 1, c]) * s_up
+            if correction is not None:
+                logit = logit + correction(sigma, r, c, logit)
             i = r * L + c
             if forced is not None:
                 bit = forced[:, r, c].astype(np.uint8)
@@ -95,16 +100,16 @@ def run_rows(rows, Jh, Jv, beta, u=None, forced=None):
     return sigma, log_q, logits
 
 
-def propose(rows, Jh, Jv, beta, S, seed, prop_base, n):
+def propose(rows, Jh, Jv, beta, S, seed, prop_base, n, correction=None):
     """S proposals of realization n with ids prop_base .. prop_base+S-1: (sigma, log_q, E, logits)."""
     L = len(rows)
     t = np.arange(S, dtype=np.uint64) + np.uint64(prop_base)
     u = philox.spin_uniforms(L, t, n, seed)
-    sigma, log_q, logits = run_rows(rows, Jh, Jv, beta, u=u)
+    sigma, log_q, logits = run_rows(rows, Jh, Jv, beta, u=u, correction=correction)
     return sigma, log_q, energy(Jh, Jv, sigma), logits
 
 
-def score(rows, Jh, Jv, beta, sigma):
+def score(rows, Jh, Jv, beta, sigma, correction=None):
     """Teacher-forced log q and energy of given configurations: (log_q, E, logits)."""
-    _, log_q, logits = run_rows(rows, Jh, Jv, beta, forced=np.asarray(sigma))
+    _, log_q, logits = run_rows(rows, Jh, Jv, beta, forced=np.asarray(sigma), correction=correction)
     return log_q, energy(Jh, Jv, sigma), logits
