@@ -187,6 +187,87 @@ tnmc_status tnmc_mh_step(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
 tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spectra,
                                  double *d_rowinfo);
 
+/* ------------------------------------------------------------------------
+ * Learned proposal correction (an extension; the paper has no counterpart).
+ * A small network Delta_i = f(x_i) of seven local features shifts each
+ * conditional logit of Eq. 5 before its draw, l_i <- l_i + Delta_i, and
+ * log q (Eq. 9) is taken from the shifted logit, so q stays a normalised
+ * distribution and the accept test of Eq. 10 keeps sampling exactly.
+ * Features of site i = (r, c), 0 where the neighbour is absent:
+ *   x0 = l_i (uncorrected logit of Eq. 5) clamped to [-32, 32]
+ *   x1 = 2 beta Jv[r-1][c] s(r-1, c)
+ *   x2 = beta Jh[r][c-1] s(r, c-1)          x3 = Jh[r][c]     x4 = Jv[r][c]
+ *   x5 = s(r-1, c+1)                        x6 = beta
+ * (Jh[r][c] joins (r,c)-(r,c+1), Jv[r][c] joins (r,c)-(r+1,c); s = +-1.)
+ * The clamp keeps the input finite where a conditional vanishes (l_i = +-inf);
+ * the corrected logit is the unclamped l_i + Delta_i.
+ * Network: x rounded to bfloat16; h1 = g(W1 x + b1) rounded to bfloat16;
+ * h2 = g(W2 h1 + b2); Delta = w3 . h2 + b3, with the smooth ReLU
+ * g(z) = 0 (z <= -1), (z + 1)^2 / 4 (|z| < 1), z (z >= 1); float32
+ * accumulation. Parameters: bfloat16 for inference, a float32 master copy for
+ * training, both in this element layout: */
+#define TNMC_MLP_FEATURES 7
+#define TNMC_MLP_IN 16          /* W1 input columns; columns 7..15 are zero */
+#define TNMC_MLP_HIDDEN 64
+#define TNMC_MLP_OFF_W1 0       /* W1 [64][16], output-major */
+#define TNMC_MLP_OFF_B1 1024    /* b1 [64] */
+#define TNMC_MLP_OFF_W2 1088    /* W2 [64][64], output-major */
+#define TNMC_MLP_OFF_B2 5184    /* b2 [64] */
+#define TNMC_MLP_OFF_W3 5248    /* w3 [64] */
+#define TNMC_MLP_OFF_B3 5312    /* b3, then 7 zeros */
+#define TNMC_MLP_PARAMS 5320
+#define TNMC_MLP_FEAT_STRIDE 8  /* floats per example row: x0 .. x6, then 0 */
+
+/* Use (enabled != 0) or stop using (enabled == 0, d_params_bf16 ignored) the
+ * correction in later tnmc_propose, tnmc_propose_static, tnmc_score,
+ * tnmc_mh_init calls of this handle. d_params_bf16: device, 16-byte aligned,
+ * TNMC_MLP_PARAMS bfloat16 values; the caller keeps it alive and unchanged
+ * while those calls' kernels run. Errors: TNMC_ERR_ARG. */
+tnmc_status tnmc_set_correction(tnmc_handle *h, const void *d_params_bf16, int32_t enabled);
+
+/* Training examples from S configurations per realization of this handle:
+ * the features of every site. d_spins: as in tnmc_score; d_logits: float32,
+ * the uncorrected logits of those configurations (tnmc_score with the
+ * diagnostic logits set and no correction); d_feat: float32
+ * [sum_n S L_n^2][TNMC_MLP_FEAT_STRIDE], in the order of d_spins.
+ * Errors: TNMC_ERR_ARG, TNMC_ERR_STATE, TNMC_ERR_CUDA. */
+tnmc_status tnmc_mlp_features(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
+                              const float *d_logits, float *d_feat);
+
+/* Floats of scratch tnmc_mlp_grad needs. */
+size_t tnmc_mlp_scratch_floats(void);
+
+/* Mean binary cross entropy of sigmoid(x0 + Delta) against the target
+ * probability sigmoid(t) and its gradient in the parameters (backpropagation,
+ * the two bfloat16 roundings passed straight through), over a minibatch.
+ * d_feat: float32 [n_ex][8]; d_target_logit: float32 [n_ex];
+ * B > 0: B examples drawn uniformly with replacement; example k is row
+ *        floor(u n_ex), u the Philox uniform of counter (k >> 2, step, 0, 3)
+ *        word k & 3 under key (seed, 0);  B == 0: all n_ex rows in order;
+ * d_params_bf16: the network; d_grad: float32 [TNMC_MLP_PARAMS] (written);
+ * d_loss: float64 [1] (written); d_scratch: float32 [tnmc_mlp_scratch_floats()];
+ * stream: a cudaStream_t. The reduction order is fixed: equal inputs give
+ * equal bits. Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+tnmc_status tnmc_mlp_grad(const float *d_feat, const float *d_target_logit, int64_t n_ex,
+                          int32_t B, uint64_t seed, int32_t step, const void *d_params_bf16,
+                          float *d_grad, double *d_loss, float *d_scratch, void *stream);
+
+/* One Adam step (Kingma & Ba, 2015, bias-corrected; step counts from 1) on the
+ * float32 master copy d_master with moments d_m, d_v (all [TNMC_MLP_PARAMS],
+ * updated in place), then the bfloat16 copy d_params_bf16 (round to nearest
+ * even). Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+tnmc_status tnmc_mlp_adam(float *d_master, float *d_m, float *d_v, const float *d_grad,
+                          int32_t step, float lr, float beta1, float beta2, float eps,
+                          void *d_params_bf16, void *stream);
+
+/* bfloat16 copy (round to nearest even) of a float32 parameter vector. */
+tnmc_status tnmc_mlp_pack(const float *d_master, void *d_params_bf16, void *stream);
+
+/* Delta of n_ex example rows (d_feat as above) by the tensor-core network of
+ * the sampler; d_delta: float32 [n_ex]. Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+tnmc_status tnmc_mlp_forward(const float *d_feat, int64_t n_ex, const void *d_params_bf16,
+                             float *d_delta, void *stream);
+
 /* Proposals without caller-provided scratch (the paper has no counterpart).
  * Same results and layouts as tnmc_propose, bit for bit, but the right
  * environments of the chains (S x sum_n L_n x chi values, 8 bytes each in

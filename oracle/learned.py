@@ -14,7 +14,7 @@ theta is.
 
 Features of site i = (r, c), in this order (0 where the neighbour is absent):
 
-    x0 = l_i                       conditional logit of the chi-MPS (Eq. 5)
+    x0 = l_i clamped to [-32, 32]  conditional logit of the chi-MPS (Eq. 5)
     x1 = 2 beta Jv[r-1, c] s(r-1, c)   field of the spin above
     x2 = beta Jh[r, c-1] s(r, c-1)     field of the spin on the left
     x3 = Jh[r, c]                  coupling to the right (spin not yet drawn)
@@ -52,6 +52,7 @@ OFF_B2 = OFF_W2 + HIDDEN * HIDDEN
 OFF_W3 = OFF_B2 + HIDDEN
 OFF_B3 = OFF_W3 + HIDDEN
 N_PARAM = OFF_B3 + 8
+LOGIT_CLAMP = 32.0
 
 
 def to_bf16(x):
@@ -117,9 +118,11 @@ def features(Jh, Jv, beta, sigma, logits):
     """
     sigma = np.asarray(sigma)
     S, L, _ = sigma.shape
+    Jh = np.asarray(Jh, dtype=np.float64)
+    Jv = np.asarray(Jv, dtype=np.float64)
     s = 2.0 * sigma.astype(np.float64) - 1.0
     X = np.zeros((S, L, L, N_FEAT))
-    X[..., 0] = np.asarray(logits, dtype=np.float64).reshape(S, L, L)
+    X[..., 0] = np.clip(np.asarray(logits, dtype=np.float64).reshape(S, L, L), -LOGIT_CLAMP, LOGIT_CLAMP)
     if L > 1:
         X[:, 1:, :, 1] = 2.0 * beta * Jv[None, :, :] * s[:, :-1, :]
         X[:, :, 1:, 2] = beta * Jh[None, :, :] * s[:, :, :-1]
@@ -197,7 +200,7 @@ class Correction:
         """Features of site (r, c) for all S chains; sigma holds the spins drawn so far."""
         S, L, _ = sigma.shape
         x = np.zeros((S, N_FEAT))
-        x[:, 0] = logit
+        x[:, 0] = np.clip(logit, -LOGIT_CLAMP, LOGIT_CLAMP)
         if r > 0:
             x[:, 1] = 2.0 * self.beta * float(self.Jv[r - 1, c]) * (2.0 * sigma[:, r - 1, c] - 1.0)
             if c < L - 1:

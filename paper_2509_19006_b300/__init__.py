@@ -26,8 +26,15 @@ EXPORTED = [
     "tnmc_status_string", "tnmc_workspace_size", "tnmc_create", "tnmc_destroy",
     "tnmc_build_envs", "tnmc_log_z", "tnmc_propose", "tnmc_score", "tnmc_mh_init",
     "tnmc_mh_step", "tnmc_set_diagnostics", "tnmc_get_device_status", "tnmc_layout_info",
-    "tnmc_propose_static", "tnmc_propose_static_limit",
+    "tnmc_propose_static", "tnmc_propose_static_limit", "tnmc_set_correction",
+    "tnmc_mlp_features", "tnmc_mlp_scratch_floats", "tnmc_mlp_grad", "tnmc_mlp_adam",
+    "tnmc_mlp_pack", "tnmc_mlp_forward",
 ]
+
+# learned proposal correction: parameter vector layout (include/tnmc.h)
+MLP_PARAMS = 5320
+MLP_OFF = {"W1": 0, "b1": 1024, "W2": 1088, "b2": 5184, "w3": 5248, "b3": 5312}
+MLP_FEAT_STRIDE = 8
 
 
 class TnmcError(RuntimeError):
@@ -77,6 +84,14 @@ def load_library():
         "tnmc_get_device_status": ([vp, vp, i32], i32),
         "tnmc_propose_static": ([vp, i32, u64, u64, vp, vp, vp], i32),
         "tnmc_propose_static_limit": ([], sz),
+        "tnmc_set_correction": ([vp, vp, i32], i32),
+        "tnmc_mlp_features": ([vp, i32, vp, vp, vp], i32),
+        "tnmc_mlp_scratch_floats": ([], sz),
+        "tnmc_mlp_grad": ([vp, vp, ctypes.c_int64, i32, u64, i32, vp, vp, vp, vp, vp], i32),
+        "tnmc_mlp_adam": ([vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, vp, vp], i32),
+        "tnmc_mlp_pack": ([vp, vp, vp], i32),
+        "tnmc_mlp_forward": ([vp, ctypes.c_int64, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -260,6 +275,40 @@ class TNMC:
                                              _ptr(ri) if ri is not None else z), "tnmc_set_diagnostics")
         return self._diag
 
+    def set_correction(self, params_bf16=None):
+        """Use the learned correction (a bfloat16 parameter tensor, see MLP) or stop (None)."""
+        if params_bf16 is None:
+            _check(self.lib.tnmc_set_correction(self.h, ctypes.c_void_p(0), 0), "tnmc_set_correction")
+            self._corr_keep = None
+            return
+        assert params_bf16.is_cuda and params_bf16.numel() == MLP_PARAMS and params_bf16.element_size() == 2
+        self._corr_keep = params_bf16
+        _check(self.lib.tnmc_set_correction(self.h, _ptr(params_bf16), 1), "tnmc_set_correction")
+
+    def score_logits(self, spins, S: int):
+        """Teacher-forced (log q, E, logits) of S configurations per realization."""
+        t = self.torch
+        saved = self._diag
+        lg = t.empty(S * self.sum_L2, dtype=t.float32, device=self.device)
+        z = ctypes.c_void_p(0)
+        _check(self.lib.tnmc_set_diagnostics(self.h, _ptr(lg), z, z), "tnmc_set_diagnostics")
+        try:
+            lq, E = self.score(spins, S)
+        finally:
+            if saved is None:
+                self.lib.tnmc_set_diagnostics(self.h, z, z, z)
+            else:
+                self.lib.tnmc_set_diagnostics(self.h, *[_ptr(x) if x is not None else z for x in saved])
+        return lq, E, lg
+
+    def mlp_features(self, spins, logits, S: int):
+        """Training features (sum_n S L_n^2, 8) of S configurations per realization."""
+        t = self.torch
+        feat = t.empty((S * self.sum_L2, MLP_FEAT_STRIDE), dtype=t.float32, device=self.device)
+        _check(self.lib.tnmc_mlp_features(self.h, int(S), _ptr(spins), _ptr(logits), _ptr(feat)),
+               "tnmc_mlp_features")
+        return feat
+
     def device_status(self, clear: bool = True):
         """(status code, per-realization flags) after synchronising the stream."""
         import numpy as np
@@ -275,3 +324,82 @@ class TNMC:
             offs.append(o)
             o += S * L * L
         return offs
+
+
+class MLP:
+    """Parameters, Adam state and buffers of the learned proposal correction on one device.
+
+    ``params`` is the float32 master copy, ``bf16`` the bfloat16 copy the sampler reads.
+    """
+
+    def __init__(self, device="cuda:0", stream=None, seed: int = 0):
+        import numpy as np
+        import torch
+        self.lib = load_library()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        # W1, W2 ~ N(0, 1/fan_in); biases and the output layer zero, so Delta starts at 0
+        rng = np.random.default_rng(seed)
+        host = np.zeros(MLP_PARAMS, np.float32)
+        W1 = np.zeros((64, 16), np.float32)
+        W1[:, :7] = rng.standard_normal((64, 7)) / np.sqrt(7.0)
+        host[0:1024] = W1.reshape(-1)
+        host[1088:5184] = (rng.standard_normal((64, 64)) / 8.0).reshape(-1)
+        self.params = torch.from_numpy(host).to(self.device)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad_buf = torch.zeros_like(self.params)
+        self.loss_buf = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self.scratch = torch.empty(int(self.lib.tnmc_mlp_scratch_floats()), dtype=torch.float32,
+                                   device=self.device)
+        self.bf16 = torch.empty(MLP_PARAMS, dtype=torch.bfloat16, device=self.device)
+        self.step = 0
+        self.pack()
+
+    def _s(self):
+        return ctypes.c_void_p(self.stream.cuda_stream)
+
+    def load(self, params_f32):
+        """Set the master copy (float32 tensor or array of MLP_PARAMS values) and its bfloat16 copy."""
+        t = self.torch
+        self.params.copy_(t.as_tensor(params_f32, dtype=t.float32))
+        self.pack()
+
+    def pack(self):
+        _check(self.lib.tnmc_mlp_pack(_ptr(self.params), _ptr(self.bf16), self._s()), "tnmc_mlp_pack")
+
+    def grad(self, feat, target_logit, batch: int = 0, seed: int = 0, step: int = 0):
+        """(gradient, loss) tensors of the mean BCE; batch 0 = every row in order."""
+        n = feat.shape[0]
+        _check(self.lib.tnmc_mlp_grad(_ptr(feat), _ptr(target_logit), int(n), int(batch), int(seed),
+                                      int(step), _ptr(self.bf16), _ptr(self.grad_buf),
+                                      _ptr(self.loss_buf), _ptr(self.scratch), self._s()),
+               "tnmc_mlp_grad")
+        return self.grad_buf, self.loss_buf
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        self.step += 1
+        _check(self.lib.tnmc_mlp_adam(_ptr(self.params), _ptr(self.m), _ptr(self.v),
+                                      _ptr(self.grad_buf), self.step, lr, beta1, beta2, eps,
+                                      _ptr(self.bf16), self._s()), "tnmc_mlp_adam")
+
+    def train(self, feat, target_logit, steps: int, batch: int, lr: float, seed: int = 0,
+              lr_final: float | None = None):
+        """Adam on minibatches drawn on the device; returns the loss of every step (tensor)."""
+        t = self.torch
+        losses = t.empty(steps, dtype=t.float64, device=self.device)
+        for k in range(steps):
+            rate = lr if lr_final is None else lr * (lr_final / lr) ** (k / max(1, steps - 1))
+            self.grad(feat, target_logit, batch, seed, self.step + 1)
+            losses[k:k + 1].copy_(self.loss_buf)
+            self.adam(rate)
+        return losses
+
+    def forward(self, feat):
+        """Delta of every feature row by the tensor-core network the sampler uses."""
+        t = self.torch
+        out = t.empty(feat.shape[0], dtype=t.float32, device=self.device)
+        _check(self.lib.tnmc_mlp_forward(_ptr(feat), int(feat.shape[0]), _ptr(self.bf16), _ptr(out),
+                                         self._s()), "tnmc_mlp_forward")
+        return out

@@ -27,6 +27,8 @@ cudaError_t launch_propose_static(const Layout &lay, int prec, int CH, int S, ui
                                   int64_t sum_L, cudaStream_t st, bool *too_big);
 int64_t static_scratch_bytes();
 int64_t sampler_smem_bytes(int prec, int CH, int L_max);
+cudaError_t launch_mlp_features(const Layout &lay, int S, int L_max, const uint8_t *spins,
+                                const float *logits, float *feat, cudaStream_t st);
 }  // namespace tnmc
 
 using namespace tnmc;
@@ -212,6 +214,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
   lay.env_slot_bytes = p.env_slot;
   lay.env_slots = p.env_slots;
   lay.samp_scratch = ws + p.off_samp;
+  lay.mlp = nullptr;
   lay.dbg_logits = nullptr;
   lay.dbg_spectra = nullptr;
   lay.dbg_rowinfo = nullptr;
@@ -240,6 +243,28 @@ tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spec
   h->lay.dbg_spectra = d_spectra;
   h->lay.dbg_rowinfo = d_rowinfo;
   return TNMC_OK;
+}
+
+tnmc_status tnmc_set_correction(tnmc_handle *h, const void *d_params_bf16, int32_t enabled) {
+  if (!h) return TNMC_ERR_ARG;
+  if (!enabled) {
+    h->lay.mlp = nullptr;
+    return TNMC_OK;
+  }
+  if (!d_params_bf16 || (reinterpret_cast<uintptr_t>(d_params_bf16) & 15) != 0) return TNMC_ERR_ARG;
+  h->lay.mlp = static_cast<const uint16_t *>(d_params_bf16);
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_mlp_features(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
+                              const float *d_logits, float *d_feat) {
+  if (!h || !d_spins || !d_logits || !d_feat || S < 1) return TNMC_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_feat) & 15) != 0) return TNMC_ERR_ARG;
+  if (!h->built) return TNMC_ERR_STATE;   // the couplings are copied in by tnmc_build_envs
+  return launch_mlp_features(h->lay, S, h->plan.L_max, d_spins, d_logits, d_feat, h->stream) ==
+                 cudaSuccess
+             ? TNMC_OK
+             : TNMC_ERR_CUDA;
 }
 
 tnmc_status tnmc_build_envs(tnmc_handle *h, const float *d_J) {

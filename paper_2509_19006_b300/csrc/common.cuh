@@ -51,6 +51,7 @@ struct Layout {
   int64_t env_slot_bytes;
   int32_t env_slots;
   void *samp_scratch;        // [max_samples * sum L][chi] of T: right environments
+  const uint16_t *mlp;       // bfloat16 parameters of the learned correction, or null (off)
   // optional diagnostics (may be null)
   float *dbg_logits;
   double *dbg_spectra;

@@ -18,6 +18,7 @@
 // tile and streams C (staged in shared memory, double-buffered) against the
 // chains' vectors (shared memory, chain-minor).
 #include "common.cuh"
+#include "mlp.cuh"
 
 #include <mutex>
 
@@ -71,7 +72,7 @@ __device__ __forceinline__ T gsum(T v) {
   return v;
 }
 
-template <typename T, int CH, bool FORCED>
+template <typename T, int CH, bool FORCED, bool CORR>
 __global__ void __launch_bounds__(SampPlan<CH>::NT)
 sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_t *in_spins,
               uint8_t *out_spins, double *out_logq, double *out_E) {
@@ -87,6 +88,11 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
   const int L = ri.L;
   const int WL = (L + 31) / 32;
   uint32_t *bits = (uint32_t *)(Vb + 2 * CH * SB);   // 2 x SB x WL
+  // learned correction (optional): staged network, per-chain logits and shifts
+  MlpSmem *mp = (MlpSmem *)(bits + 2 * SB * WL);
+  float *sh_lg = (float *)(mp + 1);
+  float *sh_dl = sh_lg + SB;
+  constexpr bool corr = CORR;   // the learned correction is on (lay.mlp != null)
   const int chi = lay.chi;
   const int tid = threadIdx.x, cg = tid % NCG, sg = tid / NCG;
   const int lane = tid & 31;
@@ -113,6 +119,7 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
 
   uint32_t *bprev = bits, *bcur = bits + SB * WL;
   for (int e = tid; e < 2 * SB * WL; e += P::NT) bits[e] = 0u;
+  if (corr) mlp_stage(mp, lay.mlp, tid, P::NT);
   bool any_bad = false;
   __syncthreads();
 
@@ -257,11 +264,11 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
       const int i = r * L + c;
       const T jup = (r > 0) ? T(jd[(r - 1) * L + c]) : T(0);
       const double jl = (c > 0) ? (double)jr[r * L + c - 1] : 0.0;
-      int sig_own[OWN];
+      T lg_own[OWN];
 #pragma unroll
       for (int o = 0; o < OWN; ++o) {
         const int j = cg + o * NCG;
-        sig_own[o] = 0;
+        lg_own[o] = T(0);
         if (j < TS) {
           const int sl = sg * TS + j;
           const int up = (r > 0) ? (bprev[sl * WL + (c >> 5)] >> (c & 31)) & 1 : 0;
@@ -274,6 +281,60 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
             logit = Num<T>::log_(rho1) - Num<T>::log_(rho0);
           }
           if (r > 0) logit += T(2) * beta * jup * T(up ? 1 : -1);
+          lg_own[o] = logit;
+          if (corr) sh_lg[sl] = act[j] ? clamp_logit((float)logit) : 0.f;
+        }
+      }
+      if (corr) {
+        // the network's shift of every chain's logit: 16 chains per warp pass
+        __syncthreads();
+        const int g = lane >> 2, t4 = lane & 3;
+        for (int m = tid >> 5; m < SB / 16; m += P::NT / 32) {
+          uint32_t xw[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int sl = 16 * m + g + 8 * h;
+            const uint32_t *bp = bprev + sl * WL, *bc = bcur + sl * WL;
+            const double sup = ((bp[c >> 5] >> (c & 31)) & 1) ? 1.0 : -1.0;
+            float f0, f1;
+            if (t4 == 0) {
+              f0 = sh_lg[sl];
+              f1 = r > 0 ? (float)(2.0 * lay.beta * (double)jd[(r - 1) * L + c] * sup) : 0.f;
+            } else if (t4 == 1) {
+              const double sle = c > 0 ? (((bc[(c - 1) >> 5] >> ((c - 1) & 31)) & 1) ? 1.0 : -1.0) : 0.0;
+              f0 = c > 0 ? (float)(lay.beta * (double)jr[r * L + c - 1] * sle) : 0.f;
+              f1 = jr[r * L + c];
+            } else if (t4 == 2) {
+              f0 = jd[r * L + c];
+              f1 = (r > 0 && c < L - 1) ? (((bp[(c + 1) >> 5] >> ((c + 1) & 31)) & 1) ? 1.f : -1.f) : 0.f;
+            } else {
+              f0 = (float)lay.beta;
+              f1 = 0.f;
+            }
+            xw[h] = pack_bf16(f0, f1);
+          }
+          const float2 d = mlp_warp16(mp, xw[0], xw[1], lane);
+          if (t4 == 0) {
+            sh_dl[16 * m + g] = d.x;
+            sh_dl[16 * m + g + 8] = d.y;
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int o = 0; o < OWN; ++o) {
+          const int j = cg + o * NCG;
+          if (j < TS) lg_own[o] += T(sh_dl[sg * TS + j]);
+        }
+      }
+      int sig_own[OWN];
+#pragma unroll
+      for (int o = 0; o < OWN; ++o) {
+        const int j = cg + o * NCG;
+        sig_own[o] = 0;
+        if (j < TS) {
+          const int sl = sg * TS + j;
+          const int up = (r > 0) ? (bprev[sl * WL + (c >> 5)] >> (c & 31)) & 1 : 0;
+          const T logit = lg_own[o];
           int sgm;
           if (FORCED) {
             sgm = act[j] ? in_spins[int64_t(S) * ri.site_off + int64_t(sid[j]) * L2 + i] : 0;
@@ -345,21 +406,30 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
 
 }  // namespace
 
-template <typename T, int CH, bool FORCED>
-static cudaError_t launch_samp_t(const Layout &lay, int S, uint64_t seed, uint64_t base,
+template <typename T, int CH, bool FORCED, bool CORR>
+static cudaError_t launch_samp_c(const Layout &lay, int S, uint64_t seed, uint64_t base,
                                  const uint8_t *in, uint8_t *out, double *lq, double *E,
                                  cudaStream_t st) {
   using P = SampPlan<CH>;
   const int WL = (lay.L_max + 31) / 32;
-  const int64_t smem = samp_smem_fixed<T, CH>() + int64_t(2) * SB * WL * 4;
+  const int64_t smem = samp_smem_fixed<T, CH>() + int64_t(2) * SB * WL * 4 +
+                       (lay.mlp ? int64_t(sizeof(MlpSmem)) + 2 * SB * 4 : 0);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(sample_kernel<T, CH, FORCED>,
+  cudaError_t e = cudaFuncSetAttribute(sample_kernel<T, CH, FORCED, CORR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const int bpr = (S + SB - 1) / SB;
-  sample_kernel<T, CH, FORCED><<<lay.n_real * bpr, P::NT, smem, st>>>(lay, S, seed, base, in, out,
-                                                                      lq, E);
+  sample_kernel<T, CH, FORCED, CORR><<<lay.n_real * bpr, P::NT, smem, st>>>(lay, S, seed, base, in,
+                                                                            out, lq, E);
   return cudaGetLastError();
+}
+
+template <typename T, int CH, bool FORCED>
+static cudaError_t launch_samp_t(const Layout &lay, int S, uint64_t seed, uint64_t base,
+                                 const uint8_t *in, uint8_t *out, double *lq, double *E,
+                                 cudaStream_t st) {
+  return lay.mlp ? launch_samp_c<T, CH, FORCED, true>(lay, S, seed, base, in, out, lq, E, st)
+                 : launch_samp_c<T, CH, FORCED, false>(lay, S, seed, base, in, out, lq, E, st);
 }
 
 template <bool FORCED>
@@ -450,7 +520,7 @@ cudaError_t launch_propose_static(const Layout &lay, int prec, int CH, int S, ui
 
 int64_t sampler_smem_bytes(int prec, int CH, int L_max) {
   const int WL = (L_max + 31) / 32;
-  const int64_t extra = int64_t(2) * SB * WL * 4;
+  const int64_t extra = int64_t(2) * SB * WL * 4 + int64_t(sizeof(MlpSmem)) + 2 * SB * 4;
   if (prec == 0) {
     switch (CH) {
       case 8: return samp_smem_fixed<double, 8>() + extra;

@@ -70,3 +70,18 @@ def test_reserved_precisions_unsupported(P):
 def test_status_strings(P):
     for code in range(8):
         assert P.status_string(code)
+
+
+def test_mlp_layout_constants_agree_with_oracle(P):
+    """The header's parameter layout of the learned correction equals the oracle's, and the binding's."""
+    from oracle import learned
+    text = open(os.path.join(ROOT, "include", "tnmc.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define (TNMC_MLP_\w+) (\d+)", text)}
+    assert defs["TNMC_MLP_FEATURES"] == learned.N_FEAT
+    assert defs["TNMC_MLP_IN"] == learned.IN_PAD and defs["TNMC_MLP_HIDDEN"] == learned.HIDDEN
+    for name in ("W1", "B1", "W2", "B2", "W3", "B3"):
+        assert defs[f"TNMC_MLP_OFF_{name}"] == getattr(learned, f"OFF_{name}"), name
+        key = {"W1": "W1", "B1": "b1", "W2": "W2", "B2": "b2", "W3": "w3", "B3": "b3"}[name]
+        assert P.MLP_OFF[key] == defs[f"TNMC_MLP_OFF_{name}"], name
+    assert defs["TNMC_MLP_PARAMS"] == learned.N_PARAM == P.MLP_PARAMS
+    assert P.load_library().tnmc_mlp_scratch_floats() > 0

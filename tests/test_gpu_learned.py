@@ -1,0 +1,268 @@
+"""GPU parity of the learned proposal correction against the oracle (through the C ABI).
+
+Tolerances. The GPU network accumulates in float32 (tensor cores, CUDA
+cores); the oracle in float64 on the same bfloat16 parameters and with the
+same two bfloat16 roundings. The float32 pre-activations of the first layer
+differ from the float64 ones by ~1e-7 relative, which moves a hidden unit
+across a bfloat16 rounding boundary with probability ~3e-5 per unit; such a
+flip changes Delta by ~1e-3. Hence: Delta agrees to 1e-5 (relative to
+1 + |Delta|) except on a small counted fraction, which agrees to 2e-2; the
+first differing draw of a free-running proposal lies within 1e-3 of the
+decision boundary; log q of equal configurations agrees to 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import parity  # noqa: E402
+from oracle import bmps, learned, philox, sampler  # noqa: E402
+from workloads import draw_bonds  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_19006_b300 import build
+    build.build()
+    import paper_2509_19006_b300 as P
+    return P
+
+
+def _net(P, seed, w3_scale=1.0):
+    """A GPU network with nonzero output layer; returns (MLP, its bfloat16 values as float64)."""
+    rng = np.random.default_rng(seed)
+    theta = learned.init_params(seed).astype(np.float64)
+    W1, b1, W2, b2, w3, b3 = learned.unpack(theta)
+    theta = learned.pack(W1, rng.standard_normal(64) * 0.5, W2, rng.standard_normal(64) * 0.5,
+                         w3_scale * rng.standard_normal(64) * 0.3, 0.2)
+    net = P.MLP(seed=seed)
+    net.load(theta.astype(np.float32))
+    torch.cuda.synchronize()
+    theta_bf = net.bf16.float().cpu().numpy().astype(np.float64)
+    return net, theta_bf
+
+
+def _examples(seed, n):
+    rng = np.random.default_rng(seed)
+    X = np.zeros((n, 8), np.float32)
+    X[:, :7] = rng.standard_normal((n, 7)) * np.array([3.0, 2.0, 2.0, 1.0, 1.0, 1.0, 0.5])
+    t = (rng.standard_normal(n) * 2.0).astype(np.float32)
+    return X, t
+
+
+def test_pack_is_round_to_nearest_even(P):
+    net, theta_bf = _net(P, 11)
+    master = net.params.cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(theta_bf, learned.to_bf16(master))
+
+
+def test_forward_matches_oracle(P):
+    net, theta_bf = _net(P, 12)
+    X, _ = _examples(13, 5000)
+    d_gpu = net.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    d_or, _ = learned.forward(theta_bf, X[:, :7].astype(np.float64), rounding=True)
+    err = np.abs(d_gpu - d_or) / (1.0 + np.abs(d_or))
+    assert np.mean(err > 1e-5) < 0.01, np.sort(err)[-20:]
+    assert err.max() < 2e-2
+    assert np.abs(d_or).mean() > 0.1          # the network is not trivial
+
+
+@pytest.mark.parametrize("n", [1, 37, 4000])
+def test_gradient_matches_oracle(P, n):
+    net, theta_bf = _net(P, 14)
+    X, t = _examples(15, n)
+    g, loss = net.grad(torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    p = 1.0 / (1.0 + np.exp(-t.astype(np.float64)))
+    l_or, g_or = learned.grad(theta_bf, X[:, :7].astype(np.float64), p, rounding=True)
+    assert abs(loss.item() - l_or) < 1e-5 * l_or
+    rel = np.linalg.norm(g - g_or) / np.linalg.norm(g_or)
+    assert rel < 2e-3, rel
+    for name, off, size in [("W2", 1088, 4096), ("w3", 5248, 64), ("b3", 5312, 1), ("W1", 0, 1024)]:
+        a, b = g[off:off + size], g_or[off:off + size]
+        assert np.linalg.norm(a - b) <= 5e-3 * np.linalg.norm(b) + 1e-9, name
+    assert not g[5313:].any()
+
+
+def test_gradient_is_deterministic_and_minibatch_rows_follow_philox(P):
+    net, _ = _net(P, 16)
+    X, t = _examples(17, 3000)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    B, seed, step = 200, 5, 9
+    g1 = net.grad(Xd, td, B, seed, step)[0].clone()
+    g2 = net.grad(Xd, td, B, seed, step)[0].clone()
+    assert torch.equal(g1, g2)
+    # the rows the kernel draws, from the oracle's Philox: word k of counter (k >> 2, step, 0, 3)
+    u = philox.to_uniform(philox.site_words(B, np.array([step]), 0, 3, seed))[0]
+    rows = np.minimum(np.floor(u * X.shape[0]).astype(np.int64), X.shape[0] - 1)
+    g3 = net.grad(torch.from_numpy(X[rows]).cuda(), torch.from_numpy(t[rows]).cuda())[0]
+    assert torch.equal(g1, g3)
+
+
+def test_adam_matches_oracle(P):
+    net, _ = _net(P, 18)
+    rng = np.random.default_rng(19)
+    g = (rng.standard_normal(P.MLP_PARAMS) * 1e-2).astype(np.float32)
+    g[5313:] = 0
+    g[np.arange(1024).reshape(64, 16)[:, 7:].reshape(-1)] = 0
+    th0 = net.params.cpu().numpy().astype(np.float64)
+    m0 = np.zeros(P.MLP_PARAMS)
+    v0 = np.zeros(P.MLP_PARAMS)
+    th, m, v = th0, m0, v0
+    for step in (1, 2, 3):
+        net.grad_buf.copy_(torch.from_numpy(g * step))
+        net.adam(1e-3)
+        th, m, v = learned.adam(th, (g * step).astype(np.float64), m, v, step, 1e-3)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(net.params.cpu().numpy(), th, rtol=1e-6, atol=1e-7)
+    np.testing.assert_array_equal(net.bf16.float().cpu().numpy(), learned.to_bf16(net.params.cpu().numpy()))
+
+
+def test_features_match_oracle(P):
+    Ls, chi, beta, S = [7, 5], 4, 1.3, 20
+    reals = parity.realizations(Ls, "gauss")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    t.build_envs(J)
+    rng = np.random.default_rng(20)
+    cfgs = [rng.integers(0, 2, (S, L, L)).astype(np.uint8) for L in Ls]
+    spins = torch.from_numpy(np.concatenate([c.reshape(-1) for c in cfgs])).cuda()
+    _, _, lg = t.score_logits(spins, S)
+    feat = t.mlp_features(spins, lg, S).cpu().numpy()
+    envs = parity.oracle_envs(reals, beta, chi)
+    o = 0
+    for (Jh, Jv), rows, c in zip(reals, envs, cfgs):
+        L = c.shape[1]
+        _, _, o_lg = sampler.score(rows, Jh, Jv, beta, c)
+        X = learned.features(Jh, Jv, beta, c, o_lg).reshape(-1, 7)
+        F = feat[o:o + S * L * L]
+        np.testing.assert_allclose(F[:, 0], X[:, 0], rtol=1e-5, atol=1e-5)
+        np.testing.assert_array_equal(F[:, 1:7], X[:, 1:7].astype(np.float32))
+        assert not F[:, 7].any()
+        o += S * L * L
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_corrected_proposals_and_scores_match_oracle(P, prec):
+    Ls, chi, beta, S, seed, base = [6, 5], 4, 1.0, 70, 42, 300
+    reals = parity.realizations(Ls, "gauss")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, prec, max_samples=S)
+    t.build_envs(J)
+    net, theta_bf = _net(P, 21, w3_scale=0.5)
+    t.set_correction(net.bf16)
+    props = t.propose(S, seed, base)
+    torch.cuda.synchronize()
+    sig = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
+    lq, E = props.logq.cpu().numpy(), props.E.cpu().numpy()
+    envs = parity.oracle_envs(reals, beta, chi)
+    band = 1e-3 if prec == "fp64" else 2e-2
+    lq_tol = 1e-4 if prec == "fp64" else 2e-3
+    n_eq = n_bd = 0
+    for n, ((Jh, Jv), rows) in enumerate(zip(reals, envs)):
+        corr = learned.Correction(theta_bf, Jh, Jv, beta)
+        o_sig, o_lq, o_E, o_lg = sampler.propose(rows, Jh, Jv, beta, S, seed, base, n, correction=corr)
+        u = philox.spin_uniforms(Jh.shape[0], np.arange(S, dtype=np.uint64) + np.uint64(base), n, seed)
+        for k in range(S):
+            a, b = sig[n][k].reshape(-1), o_sig[k].reshape(-1)
+            if np.array_equal(a, b):
+                n_eq += 1
+                assert E[n, k] == o_E[k]
+                assert abs(lq[n, k] - o_lq[k]) <= lq_tol * max(1.0, abs(o_lq[k])), (k, lq[n, k], o_lq[k])
+            else:
+                i = int(np.argmax(a != b))
+                assert abs(u[k, i] - sampler.sigmoid(o_lg[k, i])) < band, (n, k, i)
+                n_bd += 1
+        # teacher-forced: the GPU scores the oracle's proposals with the same correction
+        sp = torch.from_numpy(np.concatenate([o_sig.reshape(-1)] + [
+            np.zeros(S * L * L, np.uint8) for L in Ls[n + 1:]])).cuda()
+        if n == 0:
+            g_lq, g_E = t.score(sp, S)
+            np.testing.assert_allclose(g_lq.cpu().numpy()[0], o_lq, rtol=lq_tol, atol=lq_tol)
+            np.testing.assert_array_equal(g_E.cpu().numpy()[0], o_E)
+    assert n_eq >= 0.8 * S * len(Ls), (n_eq, n_bd)
+    status, flags = t.device_status()
+    assert status == 0 and not flags.any()
+
+
+def test_correction_off_restores_plain_sampler(P):
+    Ls, chi, beta, S = [6], 4, 1.0, 64
+    reals = parity.realizations(Ls, "pmj")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    t.build_envs(J)
+    a = t.propose(S, 3, 0)
+    a_sp, a_lq = a.spins.clone(), a.logq.clone()
+    net, _ = _net(P, 22)
+    t.set_correction(net.bf16)
+    b = t.propose(S, 3, 0)
+    assert not torch.equal(b.logq, a_lq)
+    t.set_correction(None)
+    c = t.propose(S, 3, 0)
+    assert torch.equal(c.spins, a_sp) and torch.equal(c.logq, a_lq)
+    # a zero network leaves the plain sampler's draws and log q unchanged
+    net.load(np.zeros(P.MLP_PARAMS, np.float32))
+    t.set_correction(net.bf16)
+    d = t.propose(S, 3, 0)
+    assert torch.equal(d.spins, a_sp) and torch.equal(d.logq, a_lq)
+
+
+def test_trained_correction_gains_over_plain_small_chi(P):
+    """Trained on a larger chi's conditionals, the network brings chi = 2 closer to chi = 8.
+
+    Gaussian couplings, L = 12, beta = 2 (the shape of the learned-proposal
+    workload, scaled down). Gains: the mean per-site KL divergence from the
+    chi = 8 conditionals on held-out configurations drops, and the MH
+    acceptance of the corrected chi = 2 proposal rises; MH stays exact
+    because log q is taken from the corrected logits.
+    """
+    Ls, beta, S = [12] * 16, 2.0, 256
+    reals = parity.realizations(Ls, "gauss", base_seed=5000)
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    small = P.TNMC(Ls, 2, beta, "fp64", max_samples=S)
+    big = P.TNMC(Ls, 8, beta, "fp64", max_samples=S)
+    small.build_envs(J)
+    big.build_envs(J)
+
+    def data(base):
+        props = big.propose(S, 7, base)
+        _, _, lg_s = small.score_logits(props.spins, S)
+        _, _, lg_b = big.score_logits(props.spins, S)
+        return small.mlp_features(props.spins, lg_s, S), lg_b
+
+    feat, tgt = data(0)
+    feat_te, tgt_te = data(10_000)
+    net = P.MLP(seed=3)
+
+    def kl(delta):
+        z = feat_te[:, 0].double() + delta.double()
+        zb = tgt_te.double()
+        pb = torch.sigmoid(zb)
+        ls = torch.nn.functional.logsigmoid
+        return (pb * (ls(zb) - ls(z)) + (1 - pb) * (ls(-zb) - ls(-z))).mean().item()
+
+    kl0 = kl(torch.zeros_like(tgt_te))
+    loss0 = net.grad(feat, tgt)[1].item()                  # full training set, Delta = 0
+    net.train(feat, tgt, steps=2000, batch=8192, lr=3e-3, lr_final=3e-4, seed=1)
+    loss1 = net.grad(feat, tgt)[1].item()
+    kl1 = kl(net.forward(feat_te))
+    assert loss1 < loss0, (loss0, loss1)
+    assert kl1 < 0.8 * kl0, (kl0, kl1)
+
+    def acceptance(corr, rounds=3):
+        small.set_correction(corr)
+        st = small.mh_init(9)
+        for k in range(rounds):
+            props = small.propose(S, 9, 20_000 + k * S)
+            small.mh_step(props, st, 9)
+        torch.cuda.synchronize()
+        return st.n_accept.sum().item() / (rounds * S * len(Ls))
+
+    a0 = acceptance(None)
+    a1 = acceptance(net.bf16)
+    small.set_correction(None)
+    print(f"KL per site {kl0:.4g} -> {kl1:.4g}; acceptance {a0:.4f} -> {a1:.4f}")
+    assert a1 > a0, (a0, a1)

@@ -149,6 +149,12 @@ def test_features_hand_example():
     np.testing.assert_allclose(X[0, 0], [0.0, 0, 0, 1, 1, 0, 0.5])
     # site (2, 2): above s(1,2) = +1 with Jv[1,2] = 1; left s(2,1) = +1 with Jh[2,1] = 1; no right/below
     np.testing.assert_allclose(X[2, 2], [0.8, 1.0, 0.5, 0, 0, 0, 0.5])
+    # an infinite logit (a vanished conditional) enters the network clamped to +-32
+    lg_inf = logits.copy()
+    lg_inf[0, 4] = np.inf
+    lg_inf[0, 5] = -np.inf
+    Xi = learned.features(Jh, Jv, beta, sigma, lg_inf)[0]
+    assert Xi[4, 0] == 32.0 and Xi[5, 0] == -32.0
     # the oracle sampler's per-site features equal the batch features
     corr = learned.Correction(np.zeros(learned.N_PARAM), Jh, Jv, beta)
     for r in range(3):

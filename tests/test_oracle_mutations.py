@@ -15,8 +15,8 @@ def test_dropped_up_field_is_caught(monkeypatch):
     rows = bmps.build_envs(Jh, Jv, beta, chi=2)
     orig = sampler.run_rows
 
-    def no_field(rows_, Jh_, Jv_, beta_, u=None, forced=None):
-        return orig(rows_, Jh_, np.zeros_like(Jv_), beta_, u=u, forced=forced)
+    def no_field(rows_, Jh_, Jv_, beta_, u=None, forced=None, correction=None):
+        return orig(rows_, Jh_, np.zeros_like(Jv_), beta_, u=u, forced=forced, correction=correction)
 
     sig, _, _, good = sampler.propose(rows, Jh, Jv, beta, 8, 42, 0, 0)
     ex = exact.brute_conditional_logits(Jh, Jv, beta, sig)
