@@ -89,6 +89,13 @@ typedef struct {
                             the default of the precision: 1e-12 (FP64, MIXED), 1e-6 (FP32).
                             Numerically-zero singular values must be dropped: their
                             noise directions grow under the next rows' transfer MPOs. */
+  int32_t ckpt_every;    /* 0: cache the environment of every row. K >= 2: cache only rows
+                            0, K, 2K, ... (checkpoints) plus one K-row segment, so the cache
+                            holds ceil(L/K) + K rows per realization instead of L; propose,
+                            score and mh_init then rebuild each K-row segment from the
+                            checkpoint below it before sampling it (top segment first),
+                            about one more environment build per call. Results are the same
+                            bits as with 0. Not available with TNMC_MIXED (TNMC_ERR_UNSUPPORTED). */
 } tnmc_config;
 
 typedef struct tnmc_handle tnmc_handle;

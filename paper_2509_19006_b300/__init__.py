@@ -52,6 +52,7 @@ class _Config(ctypes.Structure):
         ("prec", ctypes.c_int32),
         ("max_samples", ctypes.c_int32),
         ("cutoff", ctypes.c_double),
+        ("ckpt_every", ctypes.c_int32),
     ]
 
 
@@ -110,24 +111,25 @@ def _check(status: int, what: str):
         raise TnmcError(status, what)
 
 
-def _cfg(Ls: Sequence[int], chi: int, beta: float, prec: int, max_samples: int, cutoff: float = 0.0):
+def _cfg(Ls: Sequence[int], chi: int, beta: float, prec: int, max_samples: int, cutoff: float = 0.0,
+         ckpt_every: int = 0):
     arr = (ctypes.c_int32 * len(Ls))(*[int(x) for x in Ls])
     cfg = _Config(len(Ls), ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)), int(chi),
-                  float(beta), int(prec), int(max_samples), float(cutoff))
+                  float(beta), int(prec), int(max_samples), float(cutoff), int(ckpt_every))
     return cfg, arr
 
 
-def workspace_size(Ls, chi, beta, prec, max_samples, cutoff=0.0) -> int:
+def workspace_size(Ls, chi, beta, prec, max_samples, cutoff=0.0, ckpt_every=0) -> int:
     lib = load_library()
-    cfg, keep = _cfg(Ls, chi, beta, prec, max_samples, cutoff)
+    cfg, keep = _cfg(Ls, chi, beta, prec, max_samples, cutoff, ckpt_every)
     out = ctypes.c_size_t(0)
     _check(lib.tnmc_workspace_size(ctypes.byref(cfg), ctypes.byref(out)), "tnmc_workspace_size")
     return out.value
 
 
-def layout_info(Ls, chi, beta, prec, max_samples):
+def layout_info(Ls, chi, beta, prec, max_samples, ckpt_every=0):
     lib = load_library()
-    cfg, keep = _cfg(Ls, chi, beta, prec, max_samples)
+    cfg, keep = _cfg(Ls, chi, beta, prec, max_samples, 0.0, ckpt_every)
     a, b, c = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
     _check(lib.tnmc_layout_info(ctypes.byref(cfg), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
            "tnmc_layout_info")
@@ -161,7 +163,8 @@ class TNMC:
     DEFAULT_CUTOFF = {TNMC_FP64: 1e-12, TNMC_FP32: 1e-6, TNMC_MIXED: 1e-12}
 
     def __init__(self, Ls: Sequence[int], chi: int, beta: float, prec: str | int = "fp32",
-                 max_samples: int = 256, device="cuda:0", stream=None, cutoff: float = 0.0):
+                 max_samples: int = 256, device="cuda:0", stream=None, cutoff: float = 0.0,
+                 ckpt_every: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("TNMC needs a CUDA device; there is no CPU fallback")
@@ -176,7 +179,9 @@ class TNMC:
         self.n_real = len(self.Ls)
         self.sum_L2 = sum(L * L for L in self.Ls)
         self.cutoff = float(cutoff) if cutoff > 0 else self.DEFAULT_CUTOFF.get(self.prec, 1e-6)
-        self._cfg, self._cfg_keep = _cfg(self.Ls, chi, beta, self.prec, max_samples, self.cutoff)
+        self.ckpt_every = int(ckpt_every)
+        self._cfg, self._cfg_keep = _cfg(self.Ls, chi, beta, self.prec, max_samples, self.cutoff,
+                                         self.ckpt_every)
         nbytes = ctypes.c_size_t(0)
         _check(self.lib.tnmc_workspace_size(ctypes.byref(self._cfg), ctypes.byref(nbytes)),
                "tnmc_workspace_size")

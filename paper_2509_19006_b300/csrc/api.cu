@@ -40,7 +40,7 @@ constexpr int kEnvSlots = 148;   // concurrent realizations of the environment b
 
 struct Plan {
   int CH = 0;
-  int64_t sum_L2 = 0, sum_L = 0, sum_bonds = 0;
+  int64_t sum_L2 = 0, sum_L = 0, sum_bonds = 0, sum_cache = 0;   // sum_cache: chi x chi matrices
   int L_max = 0;
   int64_t off_reals, off_order, off_flags, off_counter, off_jr, off_jd, off_cache, off_bonds,
       off_lam, off_env, off_samp, total;
@@ -60,8 +60,12 @@ tnmc_status check_cfg(const tnmc_config *cfg) {
   if (!std::isfinite(cfg->beta) || cfg->beta < 0) return TNMC_ERR_ARG;
   if (cfg->max_samples < 1 || cfg->max_samples > (1 << 24)) return TNMC_ERR_ARG;
   if (!std::isfinite(cfg->cutoff) || cfg->cutoff >= 1.0) return TNMC_ERR_ARG;
+  if (cfg->ckpt_every < 0 || cfg->ckpt_every == 1) return TNMC_ERR_ARG;
   if (cfg->prec == TNMC_TF32 || cfg->prec == TNMC_BF16) return TNMC_ERR_UNSUPPORTED;
   if (cfg->prec != TNMC_FP64 && cfg->prec != TNMC_FP32 && cfg->prec != TNMC_MIXED) return TNMC_ERR_ARG;
+  // MIXED carries rows between builds in float64 but caches float32: a checkpoint
+  // would have to hold the float64 row; not provided
+  if (cfg->ckpt_every > 0 && cfg->prec == TNMC_MIXED) return TNMC_ERR_UNSUPPORTED;
   for (int n = 0; n < cfg->n_real; ++n)
     if (cfg->L[n] < 1 || cfg->L[n] > kMaxL) return TNMC_ERR_ARG;
   return TNMC_OK;
@@ -82,6 +86,7 @@ Plan make_plan(const tnmc_config *cfg) {
     p.sum_L2 += L * L;
     p.sum_L += L;
     p.sum_bonds += L * (L + 1);
+    p.sum_cache += cache_rows(int(L), cfg->ckpt_every) * L;
     p.L_max = std::max<int>(p.L_max, int(L));
   }
   int64_t o = 0;
@@ -92,7 +97,7 @@ Plan make_plan(const tnmc_config *cfg) {
   p.off_counter = take(64 * 4);
   p.off_jr = take(p.sum_L2 * 4);
   p.off_jd = take(p.sum_L2 * 4);
-  p.cache_bytes = p.sum_L2 * int64_t(cfg->chi) * cfg->chi * esz;
+  p.cache_bytes = p.sum_cache * int64_t(cfg->chi) * cfg->chi * esz;
   p.off_cache = take(p.cache_bytes);
   p.off_bonds = take(p.sum_bonds * 8);
   p.off_lam = take(p.sum_L * 8);
@@ -120,6 +125,29 @@ struct tnmc_handle {
   cudaStream_t stream;
   bool built = false;
 };
+
+namespace {
+
+// Run a sampler launch over all rows, or, with checkpointed environments, one
+// K-row segment at a time from the top: rebuild the segment's rows from the
+// checkpoint below it, then sample them (the chains carry over in the outputs).
+template <typename F>
+cudaError_t for_segments(tnmc_handle *h, F launch_rows) {
+  const int K = h->cfg.ckpt_every;
+  if (K <= 0) return launch_rows(h->lay);
+  const int nseg = (h->plan.L_max + K - 1) / K;
+  for (int s = 0; s < nseg; ++s) {
+    Layout l2 = h->lay;
+    l2.seg_begin = s * K;
+    l2.seg_end = s * K + K;
+    cudaError_t e = launch_env_build(l2, h->env_code, h->plan.CH, h->stream);
+    if (e == cudaSuccess) e = launch_rows(l2);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -178,7 +206,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
 
   // per-realization table and the longest-first order
   std::vector<RealInfo> reals(cfg->n_real);
-  int64_t so = 0, bo = 0, ro = 0;
+  int64_t so = 0, bo = 0, ro = 0, co = 0;
   for (int n = 0; n < cfg->n_real; ++n) {
     const int64_t L = cfg->L[n];
     reals[n].L = int32_t(L);
@@ -187,7 +215,9 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
     reals[n].bond_off = bo;
     reals[n].row_off = ro;
     reals[n].line_off = ro;
+    reals[n].cache_off = co;
     so += L * L; bo += L * (L + 1); ro += L;
+    co += cache_rows(int(L), cfg->ckpt_every) * L;
   }
   std::vector<int32_t> order(cfg->n_real);
   std::iota(order.begin(), order.end(), 0);
@@ -206,6 +236,9 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
   lay.jr = reinterpret_cast<float *>(ws + p.off_jr);
   lay.jd = reinterpret_cast<float *>(ws + p.off_jd);
   lay.cache = ws + p.off_cache;
+  lay.ckpt_every = cfg->ckpt_every;
+  lay.seg_begin = -1;
+  lay.seg_end = 0;
   lay.bonds = reinterpret_cast<int2 *>(ws + p.off_bonds);
   lay.lam = reinterpret_cast<double *>(ws + p.off_lam);
   lay.flags = reinterpret_cast<int32_t *>(ws + p.off_flags);
@@ -291,8 +324,10 @@ tnmc_status tnmc_propose(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
   if (!h || !d_spins || !d_logq || !d_E) return TNMC_ERR_ARG;
   if (S < 1 || S > h->cfg.max_samples) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
-  return launch_propose(h->lay, h->prec_code, h->plan.CH, S, seed, prop_base, d_spins, d_logq,
-                        d_E, h->stream) == cudaSuccess
+  return for_segments(h, [&](const Layout &l) {
+           return launch_propose(l, h->prec_code, h->plan.CH, S, seed, prop_base, d_spins, d_logq,
+                                 d_E, h->stream);
+         }) == cudaSuccess
              ? TNMC_OK
              : TNMC_ERR_CUDA;
 }
@@ -303,9 +338,12 @@ tnmc_status tnmc_propose_static(tnmc_handle *h, int32_t S, uint64_t seed, uint64
   if (S < 1) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
   bool too_big = false;
-  const cudaError_t e = launch_propose_static(h->lay, h->prec_code, h->plan.CH, S, seed, prop_base,
-                                              d_spins, d_logq, d_E, h->plan.sum_L, h->stream,
-                                              &too_big);
+  const int64_t esz = h->prec_code == 0 ? 8 : 4;
+  if (int64_t(S) * h->plan.sum_L * h->plan.CH * esz > static_scratch_bytes()) return TNMC_ERR_ARG;
+  const cudaError_t e = for_segments(h, [&](const Layout &l) {
+    return launch_propose_static(l, h->prec_code, h->plan.CH, S, seed, prop_base, d_spins, d_logq,
+                                 d_E, h->plan.sum_L, h->stream, &too_big);
+  });
   if (too_big) return TNMC_ERR_ARG;
   return e == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
 }
@@ -317,8 +355,9 @@ tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins, double
   if (!h || !d_spins || !d_logq || !d_E) return TNMC_ERR_ARG;
   if (S < 1 || S > h->cfg.max_samples) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
-  return launch_score(h->lay, h->prec_code, h->plan.CH, S, d_spins, d_logq, d_E, h->stream) ==
-                 cudaSuccess
+  return for_segments(h, [&](const Layout &l) {
+           return launch_score(l, h->prec_code, h->plan.CH, S, d_spins, d_logq, d_E, h->stream);
+         }) == cudaSuccess
              ? TNMC_OK
              : TNMC_ERR_CUDA;
 }
@@ -329,8 +368,10 @@ tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
   if (!h->built) return TNMC_ERR_STATE;
   cudaError_t e = launch_init_state(h->lay, seed, d_state_spins, h->stream);
   if (e == cudaSuccess)
-    e = launch_score(h->lay, h->prec_code, h->plan.CH, 1, d_state_spins, d_state_logq, d_state_E,
-                     h->stream);
+    e = for_segments(h, [&](const Layout &l) {
+      return launch_score(l, h->prec_code, h->plan.CH, 1, d_state_spins, d_state_logq, d_state_E,
+                          h->stream);
+    });
   return e == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
 }
 

@@ -54,7 +54,7 @@ __global__ void log_z_kernel(Layout lay, double *logz) {
   double *v = vsh + wib * 128, *vn = v + 64;
   const RealInfo ri = lay.reals[n];
   const int L = ri.L, chi = lay.chi;
-  const T *C0 = (const T *)lay.cache + ri.site_off * int64_t(chi) * chi;   // row 0
+  const T *C0 = (const T *)lay.cache + ri.cache_off * int64_t(chi) * chi;   // row 0 (slot 0)
   const int2 *bd = lay.bonds + ri.bond_off;                                // row 0 bonds
   for (int a = lane; a < 64; a += 32) v[a] = (a == 0) ? 1.0 : 0.0;
   __syncwarp();

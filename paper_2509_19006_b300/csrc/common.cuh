@@ -28,6 +28,7 @@ struct RealInfo {
   int64_t bond_off;   // sum_{m<n} L_m (L_m + 1): bond-dimension records before it
   int64_t row_off;    // sum_{m<n} L_m: rows before it
   int64_t line_off;   // sum_{m<n} L_m: sampler scratch lines (per sample) before it
+  int64_t cache_off;  // first chi x chi matrix of this realization in the cache
 };
 
 // Device-side view of the workspace; passed by value to every kernel.
@@ -42,7 +43,10 @@ struct Layout {
   double cutoff;             // relative singular-value cutoff of the truncation
   float *jr;                 // [sum L^2] coupling to the right neighbour (0 on the last column)
   float *jd;                 // [sum L^2] coupling to the lower neighbour (0 on the last row)
-  void *cache;               // [sum L^2][chi][chi] of T: site matrices C, row-major
+  void *cache;               // [sum rows_n L_n][chi][chi] of T: site matrices C, row-major
+  int32_t ckpt_every;        // K: 0 = every row cached; else checkpoint rows + one segment
+  int32_t seg_begin;         // rows [seg_begin, seg_end) of this launch; seg_begin < 0 = all rows
+  int32_t seg_end;
   int2 *bonds;               // [sum L (L+1)]: (even, odd) dimension of bond b of row r
   double *lam;               // [sum L]: log scale lambda_r of row r
   int32_t *flags;            // [n_real]: FLAG_* bits
@@ -117,6 +121,24 @@ __device__ __forceinline__ T log_sigmoid(T x) {
 
 __device__ __forceinline__ void set_flag(int32_t *flags, int n, int32_t bit) {
   atomicOr(flags + n, bit);
+}
+
+// Cache rows of a realization of side L. With checkpointing every K rows the
+// cache holds the checkpoint rows 0, K, 2K, ... (slot r / K) and one segment of
+// K rows (slots ceil(L/K) .. ceil(L/K) + K - 1); without it, row r is slot r.
+__host__ __device__ inline int64_t cache_rows(int L, int K) {
+  return K > 0 ? int64_t((L + K - 1) / K + K) : int64_t(L);
+}
+// Slot of row r. Full build (seg_begin < 0): checkpoint rows go to their slot,
+// the others alternate between the first two segment slots (each row is read
+// only by the row above it). Segment [a, b): its rows go to the segment slots;
+// the row below it (b, a multiple of K) is read from its checkpoint.
+__host__ __device__ inline int64_t cache_slot(int r, int L, int K, int seg_begin) {
+  if (K <= 0) return r;
+  const int64_t nck = (L + K - 1) / K;
+  if (seg_begin < 0) return (r % K == 0) ? r / K : nck + (r & 1);
+  if (r >= seg_begin && r < seg_begin + K) return nck + (r - seg_begin);
+  return r / K;
 }
 
 // Bytes rounded up to 256 for every workspace region.

@@ -401,18 +401,24 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
     const int L = ri.L;
     const float *jr = lay.jr + ri.site_off;
     const float *jd = lay.jd + ri.site_off;
-    TS *cache_n = (TS *)lay.cache + ri.site_off * chi2;
+    TS *cache_n = (TS *)lay.cache + ri.cache_off * chi2;
+    // rows of this launch: all (bottom-up), or one segment [a, b) rebuilt from
+    // the checkpoint of row b (from the bottom row when b = L)
+    const int K = lay.ckpt_every;
+    const int r_lo = lay.seg_begin < 0 ? 0 : lay.seg_begin;
+    const int r_hi = lay.seg_begin < 0 ? L - 1 : min(lay.seg_end, L) - 1;
+    if (r_lo > r_hi) continue;   // uniform: this realization has no row in the segment
     int2 *bonds_n = lay.bonds + ri.bond_off;
     if (lay.flags[n] & FLAG_BAD_J) continue;  // uniform: read by all threads after the barrier
 
-    if (tid == 0) sh_lam = 0.0;
-    for (int r = L - 1; r >= 0; --r) {
+    if (tid == 0) sh_lam = (r_hi < L - 1) ? lay.lam[ri.row_off + r_hi + 1] : 0.0;
+    for (int r = r_hi; r >= r_lo; --r) {
       const bool trivial_prev = (r == L - 1);
       // the previous row in the build's own precision
       const TC *cprev = P::split_carry ? carry + int64_t((r + 1) & 1) * L * chi2
-                                       : (const TC *)(cache_n + int64_t(r + 1) * L * chi2);
+                                       : (const TC *)(cache_n + cache_slot(r + 1, L, K, lay.seg_begin) * L * chi2);
       TC *ccur = P::split_carry ? carry + int64_t(r & 1) * L * chi2 : nullptr;
-      TS *dst_row = cache_n + int64_t(r) * L * chi2;
+      TS *dst_row = cache_n + cache_slot(r, L, K, lay.seg_begin) * L * chi2;
       const int2 *bprev = bonds_n + int64_t(r + 1) * (L + 1);
       // ---- row constants: sum log cosh(beta Jh) + sum log 2 cosh(beta Jv) (row r < L-1)
       {

@@ -98,7 +98,12 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
   const int lane = tid & 31;
   const int gbase = lane - cg;                  // first lane of this chain group
   const float *jr = lay.jr + ri.site_off, *jd = lay.jd + ri.site_off;
-  const T *cache_n = (const T *)lay.cache + ri.site_off * int64_t(chi) * chi;
+  const T *cache_n = (const T *)lay.cache + ri.cache_off * int64_t(chi) * chi;
+  // rows of this launch: all, or one segment [r_begin, r_end) whose chains
+  // continue from the spins, log q and energies written by the segment above
+  const int r_begin = lay.seg_begin < 0 ? 0 : lay.seg_begin;
+  const int r_end = lay.seg_begin < 0 ? L : min(lay.seg_end, L);
+  if (r_begin >= r_end) return;   // uniform over the CTA: no row of this realization
   const int2 *bonds_n = lay.bonds + ri.bond_off;
   T *rs = (T *)lay.samp_scratch + ri.line_off * int64_t(lay.max_samples) * CH;
   const int64_t L2 = int64_t(L) * L;
@@ -122,10 +127,27 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
   if (corr) mlp_stage(mp, lay.mlp, tid, P::NT);
   bool any_bad = false;
   __syncthreads();
+  if (r_begin > 0) {
+    // resume: the row above from the spins written (or given) so far, and the sums
+    const uint8_t *sp = FORCED ? in_spins : out_spins;
+#pragma unroll
+    for (int o = 0; o < OWN; ++o) {
+      const int j = cg + o * NCG;
+      if (j < TS && act[j]) {
+        const uint8_t *row = sp + int64_t(S) * ri.site_off + int64_t(sid[j]) * L2 + int64_t(r_begin - 1) * L;
+        uint32_t *bw = bprev + (sg * TS + j) * WL;
+        for (int c = 0; c < L; ++c)
+          if (row[c]) bw[c >> 5] |= 1u << (c & 31);
+        lq[o] = out_logq[int64_t(n) * S + sid[j]];
+        en[o] = out_E[int64_t(n) * S + sid[j]];
+      }
+    }
+    __syncthreads();
+  }
 
-  for (int r = 0; r < L; ++r) {
+  for (int r = r_begin; r < r_end; ++r) {
     const int2 *bd = bonds_n + int64_t(r) * (L + 1);
-    const T *crow = cache_n + int64_t(r) * L * chi * chi;
+    const T *crow = cache_n + cache_slot(r, L, lay.ckpt_every, lay.seg_begin) * L * chi * chi;
     // chain-owner lanes clear this row's bits
 #pragma unroll
     for (int o = 0; o < OWN; ++o) {

@@ -85,3 +85,19 @@ def test_mlp_layout_constants_agree_with_oracle(P):
         assert P.MLP_OFF[key] == defs[f"TNMC_MLP_OFF_{name}"], name
     assert defs["TNMC_MLP_PARAMS"] == learned.N_PARAM == P.MLP_PARAMS
     assert P.load_library().tnmc_mlp_scratch_floats() > 0
+
+
+def test_checkpointing_fits_the_L1024_workload(P):
+    """64 realizations at L = 1024, chi = 32, S = 128 in float32: the full cache alone is
+    275 GB; with a checkpoint every 32 rows the whole workspace is about 20 GB."""
+    Ls = [1024] * 64
+    cache_full, _, _ = P.layout_info(Ls, 32, 3.0, P.TNMC_FP32, 128)
+    assert cache_full == 64 * 1024 * 1024 * 32 * 32 * 4
+    cache_ck, _, samp = P.layout_info(Ls, 32, 3.0, P.TNMC_FP32, 128, ckpt_every=32)
+    assert cache_ck == 64 * (32 + 32) * 1024 * 32 * 32 * 4
+    assert P.workspace_size(Ls, 32, 3.0, P.TNMC_FP32, 128, ckpt_every=32) < 21e9
+    with pytest.raises(P.TnmcError):
+        P.workspace_size(Ls, 32, 3.0, P.TNMC_FP32, 128, ckpt_every=1)
+    with pytest.raises(P.TnmcError) as e:
+        P.workspace_size(Ls, 32, 3.0, P.TNMC_MIXED, 128, ckpt_every=32)
+    assert e.value.status == 7

@@ -1,0 +1,63 @@
+"""Checkpointed environments (every K-th row cached, segments rebuilt before sampling)
+give the same bits as the fully cached environments, through the C ABI."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import parity  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_19006_b300 import build
+    build.build()
+    import paper_2509_19006_b300 as P
+    return P
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("K", [2, 3, 5])
+def test_checkpointed_equals_full_cache(P, prec, K):
+    Ls, chi, beta, S = [9, 6, 12], 4, 1.5, 70
+    reals = parity.realizations(Ls, "gauss")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    full = P.TNMC(Ls, chi, beta, prec, max_samples=S)
+    ck = P.TNMC(Ls, chi, beta, prec, max_samples=S, ckpt_every=K)
+    assert ck.ws_bytes < full.ws_bytes or K >= 5
+    for t in (full, ck):
+        t.build_envs(J)
+    assert torch.equal(full.log_z(), ck.log_z())
+    a, b = full.propose(S, 42, 100), ck.propose(S, 42, 100)
+    assert torch.equal(a.spins, b.spins) and torch.equal(a.logq, b.logq) and torch.equal(a.E, b.E)
+    la, Ea = full.score(a.spins, S)
+    lb, Eb = ck.score(a.spins, S)
+    assert torch.equal(la, lb) and torch.equal(Ea, Eb)
+    sa, sb = full.mh_init(5), ck.mh_init(5)
+    assert torch.equal(sa.spins, sb.spins) and torch.equal(sa.logq, sb.logq)
+    acc_a, acc_b = full.mh_step(a, sa, 5), ck.mh_step(b, sb, 5)
+    assert torch.equal(acc_a, acc_b) and torch.equal(sa.n_accept, sb.n_accept)
+    c, d = full.propose_static(S, 43, 7), ck.propose_static(S, 43, 7)
+    assert torch.equal(c.spins, d.spins) and torch.equal(c.logq, d.logq)
+    # with the learned correction on
+    net = P.MLP(seed=1)
+    net.params[5248:5312] = 0.2
+    net.pack()
+    full.set_correction(net.bf16)
+    ck.set_correction(net.bf16)
+    e, f = full.propose(S, 44, 0), ck.propose(S, 44, 0)
+    assert torch.equal(e.spins, f.spins) and torch.equal(e.logq, f.logq)
+    for t in (full, ck):
+        st, flags = t.device_status()
+        assert st == 0 and not flags.any()
+
+
+def test_checkpoint_argument_checks(P):
+    with pytest.raises(P.TnmcError):
+        P.TNMC([8], 4, 1.0, "fp32", max_samples=4, ckpt_every=1)
+    with pytest.raises(P.TnmcError) as e:
+        P.TNMC([8], 4, 1.0, "mixed", max_samples=4, ckpt_every=4)
+    assert e.value.status == 7
