@@ -7,7 +7,13 @@ scan (Sec. 3.2-3.4, Eq. 10). Default workload: 64 +-J realizations at L = 256,
 beta = 3, chi = 64, S = 256 (the accepted-samples/s workload).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|fp32|mixed]
-                    [--impl ours|reference] [--workload L256]
+                    [--impl ours|reference] [--workload L256|gauss128|L1024|...]
+                    [--learned [--teacher-chi 32] [--train-steps 4000]] [--ckpt K]
+
+--learned trains the learned proposal correction before the timed region (on
+configurations of a chi = teacher-chi handle and both handles' conditionals)
+and times steps whose proposals carry the correction; the line reports the
+training time and the plain / corrected / teacher acceptance.
 
 Under torchrun (N > 1) each rank runs its own batch of the same size with its
 own disorder seeds (weak scaling, no collective on the data path); rank 0
@@ -31,7 +37,9 @@ sys.path.insert(0, ROOT)
 
 from workloads import SAMPLING_SEED, config  # noqa: E402
 
-METRIC = "accepted samples/s at L=256,chi=64 (end to end: environments + proposals + MH)"
+def metric_name(wl) -> str:
+    return (f"accepted samples/s at L={wl.Ls[0]},chi={wl.chi} "
+            "(end to end: environments + proposals + MH)")
 FP64_NOMINAL_GFLOPS = 1250.0          # B300 float64 (recipe table)
 FP32_PEAK_GFLOPS = 148 * 128 * 2 * 2.032  # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
 
@@ -153,7 +161,7 @@ def run_reference(args, wl):
     sample = (f"realization 0 of {wl.name}: bottom {rows_done} environment rows timed, "
               f"per-row cost extrapolated to all {wl.Ls[0]} rows; proposals not timed; "
               f"acceptance {args.ref_acceptance} taken from the GPU run")
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "accepted/s",
+    line = {"impl": "reference", "metric": metric_name(wl), "value": v, "unit": "accepted/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl.name, "realizations": 1},
@@ -165,6 +173,60 @@ def run_reference(args, wl):
 
 
 # ----------------------------------------------------------------------- our arm
+def train_correction(P, t, J, wl, args, dev):
+    """Train the learned correction of handle t (setup, outside the timed region).
+
+    Data: S configurations per realization drawn by a chi = args.teacher_chi
+    handle, scored by both handles (their conditional logits); the network is
+    trained on t's features against the teacher's logits, then installed in t.
+    Returns the training summary, with plain / corrected / teacher acceptance
+    of one extra MH pass each.
+    """
+    import torch
+    S = wl.S
+    t0 = time.perf_counter()
+    teacher = P.TNMC(wl.Ls, args.teacher_chi, wl.beta, args.prec, max_samples=S, device=dev,
+                     cutoff=args.cutoff)
+    t.build_envs(J)
+    teacher.build_envs(J)
+    props = teacher.propose(S, 7, 0)
+    _, _, lg_s = t.score_logits(props.spins, S)
+    _, _, lg_b = teacher.score_logits(props.spins, S)
+    feat = t.mlp_features(props.spins, lg_s, S)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = P.MLP(device=dev, stream=t.stream, seed=3)
+    t1 = time.perf_counter()
+    net.train(feat, lg_b, steps=args.train_steps, batch=65536, lr=3e-3, lr_final=3e-4, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+
+    def acceptance(h, corr):
+        """Accept rate of a second round of S proposals per chain (the first round starts it)."""
+        h.set_correction(corr)
+        st = h.mh_init_empty()
+        pr = h.propose(S, 11, 5_000_000)
+        h.mh_step(pr, st, 11)
+        n0 = st.n_accept.sum().item()
+        pr = h.propose(S, 11, 5_000_000 + S)
+        h.mh_step(pr, st, 11)
+        torch.cuda.synchronize()
+        return (st.n_accept.sum().item() - n0) / (S * wl.n_real)
+
+    a_plain = acceptance(t, None)
+    a_teacher = acceptance(teacher, None)
+    a_corr = acceptance(t, net.bf16)
+    del feat, lg_s, lg_b, props, teacher
+    torch.cuda.empty_cache()
+    t.set_correction(net.bf16)
+    t._net_keep = net
+    return {"teacher_chi": args.teacher_chi, "train_steps": args.train_steps, "batch": 65536,
+            "examples": S * sum(L * L for L in wl.Ls),
+            "data_s": t_data, "train_s": t_train,
+            "acceptance_plain": a_plain, "acceptance_corrected": a_corr,
+            "acceptance_teacher": a_teacher}
+
+
 def run_ours(args, wl):
     import torch
     import paper_2509_19006_b300 as P
@@ -180,8 +242,13 @@ def run_ours(args, wl):
     Jhost = torch.from_numpy(wl.packed_J()).pin_memory()
     J = Jhost.to(dev)
     S = wl.S
-    t = P.TNMC(wl.Ls, wl.chi, wl.beta, args.prec, max_samples=S, device=dev, cutoff=args.cutoff)
+    ckpt = args.ckpt if args.ckpt >= 0 else (32 if max(wl.Ls) >= 1024 else 0)
+    t = P.TNMC(wl.Ls, wl.chi, wl.beta, args.prec, max_samples=S, device=dev, cutoff=args.cutoff,
+               ckpt_every=ckpt)
     stream = t.stream
+    learned = None
+    if args.learned:
+        learned = train_correction(P, t, J, wl, args, dev)
     props = t.alloc_proposals(S)
     state = None
     acc = torch.empty((wl.n_real, S), dtype=torch.uint8, device=dev)
@@ -194,7 +261,9 @@ def run_ours(args, wl):
         t.log_z(out=logz)
         t.propose(S, SAMPLING_SEED, base, out=props)
         if state is None:
-            state = t.mh_init(SAMPLING_SEED)
+            # the chain starts at its first proposal: a uniformly random start can have
+            # q = 0 in float32 arithmetic (an unlikely forced spin's conditional cancels to 0)
+            state = t.mh_init_empty()
         t.mh_step(props, state, SAMPLING_SEED, accept=acc)
 
     # warm-up (the first one also gathers the algorithmic flop count of the build)
@@ -214,7 +283,7 @@ def run_ours(args, wl):
 
     # ---------------- device-resident timed region
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    env_ms, step_ms, accepted = [], [], 0
+    env_ms, step_ms, prop_ms, accepted = [], [], [], 0
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
@@ -226,16 +295,18 @@ def run_ours(args, wl):
         t_all0.record(stream)
         for k in range(args.steps):
             flush.zero_()
-            e0, e1, e2 = ev(), ev(), ev()
+            e0, e1, e2, e3 = ev(), ev(), ev(), ev()
             e0.record(stream)
             t.build_envs(J)
             e1.record(stream)
             t.log_z(out=logz)
             t.propose(S, SAMPLING_SEED, 10_000_000 * (k + 1), out=props)
+            e3.record(stream)
             t.mh_step(props, state, SAMPLING_SEED, accept=acc)
             e2.record(stream)
             env_ms.append((e0, e1))
             step_ms.append((e0, e2))
+            prop_ms.append((e1, e3))
         t_all1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -243,6 +314,7 @@ def run_ours(args, wl):
     clk = clocks.stop()
     accepted = int((state.n_accept - n_acc0).sum().item())
     env_t = [a.elapsed_time(b) for a, b in env_ms]
+    prop_t = [a.elapsed_time(b) for a, b in prop_ms]
     step_t = [a.elapsed_time(b) for a, b in step_ms]
     total_ms = t_all0.elapsed_time(t_all1)   # includes the L2 flushes between steps
     my_ms = sum(step_t)
@@ -299,21 +371,26 @@ def run_ours(args, wl):
                               f"rows timed and extrapolated to {wl.Ls[0]} rows (proposals not timed); "
                               f"acceptance taken from this run ({acc_rate:.4f})")}
         line = {
-            "metric": METRIC,
+            "metric": metric_name(wl),
             "value": accepted_all / (my_ms_all / 1e3),
             "unit": "accepted/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": my_ms_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f64 build + f32 sampling"}[args.prec],
-            "data": "synthetic +-J disorder (p = 1/2), seeded",
+            "data": ("synthetic Gaussian N(0,1) disorder, seeded" if wl.kind == "gauss"
+                     else "synthetic +-J disorder (p = 1/2), seeded"),
             "config": {"workload": wl.name, "L": wl.Ls[0], "chi": wl.chi, "beta": wl.beta,
                        "realizations_per_gpu": wl.n_real, "samples_per_realization": S,
-                       "precision": args.prec, "cutoff": t.cutoff,
+                       "precision": args.prec, "cutoff": t.cutoff, "ckpt_every": ckpt,
+                       "learned_correction": bool(args.learned),
                        "l2": "flushed (256 MB write) before every timed step; environment cache >> L2"},
             "acceptance": accepted / proposals,
             "proposals_per_s": proposals * world / (my_ms_all / 1e3),
             "env_build_ms": env_avg_s * 1e3,
+            "step_breakdown_ms": {"env_build": env_avg_s * 1e3,
+                                  "log_z_and_proposals": sum(prop_t) / len(prop_t),
+                                  "mh": my_ms / args.steps - env_avg_s * 1e3 - sum(prop_t) / len(prop_t)},
             "bond_dim_mean": dmean,
             "roofline": {"kernel": "env_build_kernel (boundary-MPS build)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
@@ -323,10 +400,13 @@ def run_ours(args, wl):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_acc_all / e2e_s_all, "unit": "accepted/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * (2 + 1 + 1 + 1),
+            "gpu_launches": args.steps * (2 + 1 + 1 + 1 + (2 * ((max(wl.Ls) + ckpt - 1) // ckpt) - 1
+                                                          if ckpt else 0)),
             "clocks": clk,
             "hbm_gbs_measured": peaks.get("hbm_gbs"),
         }
+        if learned is not None:
+            line["learned"] = learned
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -360,6 +440,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--ref-acceptance", type=float, default=1.0)
+    ap.add_argument("--ckpt", type=int, default=-1,
+                    help="cache every K-th environment row (default: 32 for L >= 1024, else off)")
+    ap.add_argument("--learned", action="store_true",
+                    help="train the learned correction (setup) and time the corrected steps")
+    ap.add_argument("--teacher-chi", type=int, default=32)
+    ap.add_argument("--train-steps", type=int, default=4000)
     ap.add_argument("--env-once", action="store_true",
                     help="build the environments once and exit (for profiler captures)")
     args = ap.parse_args()

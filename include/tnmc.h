@@ -161,6 +161,16 @@ tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
 tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
                          double *d_state_logq, double *d_state_E);
 
+/* A chain state with no configuration yet: spins 0, E = 0 and log q = +inf,
+ * so that the first proposal of the next tnmc_mh_step has log r = +inf and is
+ * accepted: the chain then starts at a draw of q (the paper has no
+ * counterpart). Use it where the random state of tnmc_mh_init can have
+ * q = 0 in the arithmetic: in float32, the conditional of an unlikely forced
+ * spin cancels to exactly 0 and such a chain would reject forever.
+ * The forced first acceptance is counted in d_n_accept. */
+tnmc_status tnmc_mh_init_empty(tnmc_handle *h, uint8_t *d_state_spins, double *d_state_logq,
+                               double *d_state_E);
+
 /* Independence Metropolis-Hastings (Eq. 10) over S proposals per
  * realization, consumed in id order prop_base .. prop_base + S - 1: proposal
  * t is accepted iff log u_t < (-beta E' - log q') - (-beta E - log q).

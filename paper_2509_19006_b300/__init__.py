@@ -28,7 +28,7 @@ EXPORTED = [
     "tnmc_mh_step", "tnmc_set_diagnostics", "tnmc_get_device_status", "tnmc_layout_info",
     "tnmc_propose_static", "tnmc_propose_static_limit", "tnmc_set_correction",
     "tnmc_mlp_features", "tnmc_mlp_scratch_floats", "tnmc_mlp_grad", "tnmc_mlp_adam",
-    "tnmc_mlp_pack", "tnmc_mlp_forward",
+    "tnmc_mlp_pack", "tnmc_mlp_forward", "tnmc_mh_init_empty",
 ]
 
 # learned proposal correction: parameter vector layout (include/tnmc.h)
@@ -80,6 +80,7 @@ def load_library():
         "tnmc_propose": ([vp, i32, u64, u64, vp, vp, vp], i32),
         "tnmc_score": ([vp, i32, vp, vp, vp], i32),
         "tnmc_mh_init": ([vp, u64, vp, vp, vp], i32),
+        "tnmc_mh_init_empty": ([vp, vp, vp, vp], i32),
         "tnmc_mh_step": ([vp, i32, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "tnmc_set_diagnostics": ([vp, vp, vp, vp], i32),
         "tnmc_get_device_status": ([vp, vp, i32], i32),
@@ -256,6 +257,17 @@ class TNMC:
                         t.zeros(self.n_real, dtype=t.int64, device=self.device))
         _check(self.lib.tnmc_mh_init(self.h, int(seed), _ptr(st.spins), _ptr(st.logq), _ptr(st.E)),
                "tnmc_mh_init")
+        return st
+
+    def mh_init_empty(self) -> ChainState:
+        """A chain without a configuration: the first proposal of the next mh_step is accepted."""
+        t = self.torch
+        st = ChainState(t.empty(self.sum_L2, dtype=t.uint8, device=self.device),
+                        t.empty(self.n_real, dtype=t.float64, device=self.device),
+                        t.empty(self.n_real, dtype=t.float64, device=self.device),
+                        t.zeros(self.n_real, dtype=t.int64, device=self.device))
+        _check(self.lib.tnmc_mh_init_empty(self.h, _ptr(st.spins), _ptr(st.logq), _ptr(st.E)),
+               "tnmc_mh_init_empty")
         return st
 
     def mh_step(self, props: Proposals, state: ChainState, seed: int, accept=None):

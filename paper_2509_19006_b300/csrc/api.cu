@@ -14,6 +14,7 @@ cudaError_t launch_ingest(const Layout &lay, const float *J, cudaStream_t st);
 cudaError_t launch_env_build(const Layout &lay, int mode, int CH, cudaStream_t st);
 cudaError_t launch_log_z(const Layout &lay, int prec, double *logz, cudaStream_t st);
 cudaError_t launch_init_state(const Layout &lay, uint64_t seed, uint8_t *spins, cudaStream_t st);
+cudaError_t launch_empty_state(const Layout &lay, double *logq, double *E, cudaStream_t st);
 cudaError_t launch_mh(const Layout &lay, int S, uint64_t seed, uint64_t base, const uint8_t *ps,
                       const double *pl, const double *pe, uint8_t *ss, double *sl, double *se,
                       uint8_t *acc, int64_t *nacc, cudaStream_t st);
@@ -372,6 +373,14 @@ tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
       return launch_score(l, h->prec_code, h->plan.CH, 1, d_state_spins, d_state_logq, d_state_E,
                           h->stream);
     });
+  return e == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_mh_init_empty(tnmc_handle *h, uint8_t *d_state_spins, double *d_state_logq,
+                               double *d_state_E) {
+  if (!h || !d_state_spins || !d_state_logq || !d_state_E) return TNMC_ERR_ARG;
+  cudaError_t e = cudaMemsetAsync(d_state_spins, 0, size_t(h->plan.sum_L2), h->stream);
+  if (e == cudaSuccess) e = launch_empty_state(h->lay, d_state_logq, d_state_E, h->stream);
   return e == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
 }
 

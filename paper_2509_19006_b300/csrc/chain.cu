@@ -154,6 +154,21 @@ cudaError_t launch_log_z(const Layout &lay, int prec, double *logz, cudaStream_t
   return cudaGetLastError();
 }
 
+// A chain with no state yet: log q = +inf makes log r = +inf for the first
+// proposal, which is therefore accepted, so the chain starts at a draw of q.
+__global__ void empty_state_kernel(int n_real, double *logq, double *E) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < n_real) {
+    logq[n] = __longlong_as_double(0x7ff0000000000000ll);   // +inf
+    E[n] = 0.0;
+  }
+}
+
+cudaError_t launch_empty_state(const Layout &lay, double *logq, double *E, cudaStream_t st) {
+  empty_state_kernel<<<(lay.n_real + 255) / 256, 256, 0, st>>>(lay.n_real, logq, E);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_state(const Layout &lay, uint64_t seed, uint8_t *spins, cudaStream_t st) {
   init_state_kernel<<<lay.n_real, 256, 0, st>>>(lay, seed, spins);
   return cudaGetLastError();

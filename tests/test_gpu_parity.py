@@ -98,53 +98,95 @@ def test_score_matches_propose(P, prec):
 
 
 def test_fp64_energies_exact_and_oracle_scoring(P):
+    """The GPU scores the oracle's proposals: exact energies, log q to 1e-9."""
     Ls, chi, beta, S = [12], 6, 2.0, 128
-    t, reals, lz, props, _, _, _ = _run(P, Ls, chi, beta, "fp64", "pmj", S, prop_base=12345)
-    Jh, Jv = reals[0]
-    sig = parity.split_spins(props.spins.cpu().numpy(), Ls, S)[0]
-    np.testing.assert_array_equal(props.E.cpu().numpy()[0], energy(Jh, Jv, sig))
+    reals = parity.realizations(Ls, "pmj")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    t.build_envs(J)
+    (Jh, Jv), = reals
     rows = bmps.build_envs(Jh, Jv, beta, chi)
-    o_lq, _, _ = sampler.score(rows, Jh, Jv, beta, sig)
-    np.testing.assert_allclose(props.logq.cpu().numpy()[0], o_lq, rtol=0, atol=1e-9)
+    o_sig, o_lq, o_E, _ = sampler.propose(rows, Jh, Jv, beta, S, 42, 12345, 0)
+    np.testing.assert_array_equal(o_E, energy(Jh, Jv, o_sig))
+    g_lq, g_E = t.score(torch.from_numpy(o_sig.reshape(-1)).cuda(), S)
+    np.testing.assert_array_equal(g_E.cpu().numpy()[0], o_E)
+    np.testing.assert_allclose(g_lq.cpu().numpy()[0], o_lq, rtol=0, atol=1e-9)
+
+
+def _oracle_proposals_on_gpu(P, t, Ls, reals, envs, beta, S, seed, base):
+    """The oracle's proposals of every realization, and the same arrays as GPU inputs."""
+    out = [sampler.propose(rows, Jh, Jv, beta, S, seed, base, n)[:3]
+           for n, ((Jh, Jv), rows) in enumerate(zip(reals, envs))]
+    spins = torch.from_numpy(np.concatenate([o[0].reshape(-1) for o in out])).cuda()
+    logq = torch.from_numpy(np.stack([o[1] for o in out])).cuda()
+    E = torch.from_numpy(np.stack([o[2] for o in out])).cuda()
+    return out, P.Proposals(spins, logq, E, S, base)
 
 
 def test_fp64_mh_chain_bit_exact(P):
+    """The GPU chain on the oracle's proposals takes the oracle chain's decisions.
+
+    The initial state is the GPU's (its spins and score checked against the
+    oracle first); the proposals fed to both chains are the oracle's own.
+    """
     Ls, chi, beta, S = [8, 5], 4, 1.0, 200
     reals = parity.realizations(Ls, "pmj")
     J = torch.from_numpy(parity.packed_J(reals)).cuda()
     t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
     t.build_envs(J)
     state = t.mh_init(seed=7)
-    s0 = parity.split_spins(state.spins.cpu().numpy(), Ls, 1)
-    s0_lq, s0_E = state.logq.cpu().numpy().copy(), state.E.cpu().numpy().copy()
     envs = parity.oracle_envs(reals, beta, chi)
+    o_state = []
+    g0 = parity.split_spins(state.spins.cpu().numpy(), Ls, 1)
+    g_lq, g_E = state.logq.cpu().numpy(), state.E.cpu().numpy()
     for n, (L, (Jh, Jv), rows) in enumerate(zip(Ls, reals, envs)):
-        np.testing.assert_array_equal(s0[n][0], philox.init_spins(L, n, 7))
-        o_lq, o_E, _ = sampler.score(rows, Jh, Jv, beta, s0[n])
-        assert s0_E[n] == o_E[0]
-        assert abs(s0_lq[n] - o_lq[0]) < 1e-9
+        s0 = philox.init_spins(L, n, 7)
+        np.testing.assert_array_equal(g0[n][0], s0)
+        o_lq, o_E, _ = sampler.score(rows, Jh, Jv, beta, s0[None])
+        assert g_E[n] == o_E[0]
+        assert abs(g_lq[n] - o_lq[0]) < 1e-9
+        o_state.append((s0, float(o_lq[0]), float(o_E[0])))
+    # both chains continue from the oracle's state value (equal to the GPU's to 1e-9)
+    state.logq.copy_(torch.tensor([o[1] for o in o_state], dtype=torch.float64))
     total_acc = 0
     for step in range(2):
         base = 1000 * step
-        props = t.propose(S, seed=7, prop_base=base)
-        acc = t.mh_step(props, state, seed=7).cpu().numpy()
-        psig = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
-        plq, pE = props.logq.cpu().numpy(), props.E.cpu().numpy()
-        for n, (L, (Jh, Jv), rows) in enumerate(zip(Ls, reals, envs)):
-            st_in = (s0[n][0], s0_lq[n], s0_E[n])
-            # the oracle chain on the GPU's own proposals: same accept decisions
-            (o_sig, o_lq, o_E), o_acc, o_lr, o_u = mh.chain(st_in, (psig[n], plq[n], pE[n]), beta, 7, base, n)
-            near = np.abs(np.log(o_u) - o_lr) < 1e-9
+        o_props, g_props = _oracle_proposals_on_gpu(P, t, Ls, reals, envs, beta, S, 7, base)
+        acc = t.mh_step(g_props, state, seed=7).cpu().numpy()
+        for n in range(len(Ls)):
+            (o_sig, o_lq, o_E), o_acc, o_lr, o_u = mh.chain(o_state[n], o_props[n], beta, 7, base, n)
+            near = np.abs(np.log(o_u) - o_lr) < 1e-12
             assert np.array_equal(acc[n][~near], o_acc[~near])
             total_acc += int(acc[n].sum())
-            s0[n][0], s0_lq[n], s0_E[n] = o_sig, o_lq, o_E
+            o_state[n] = (o_sig, o_lq, o_E)
         torch.cuda.synchronize()
         g_sig = parity.split_spins(state.spins.cpu().numpy(), Ls, 1)
         for n in range(len(Ls)):
-            np.testing.assert_array_equal(g_sig[n][0], s0[n][0])
-            assert state.E.cpu().numpy()[n] == s0_E[n]
+            np.testing.assert_array_equal(g_sig[n][0], o_state[n][0])
+            assert state.E.cpu().numpy()[n] == o_state[n][2]
+            assert state.logq.cpu().numpy()[n] == o_state[n][1]
     assert state.n_accept.cpu().numpy().sum() == total_acc
     assert total_acc > 0
+
+
+def test_mh_from_empty_state_starts_at_first_proposal(P):
+    Ls, chi, beta, S = [7, 4], 4, 1.2, 50
+    reals = parity.realizations(Ls, "gauss")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    t.build_envs(J)
+    envs = parity.oracle_envs(reals, beta, chi)
+    state = t.mh_init_empty()
+    o_props, g_props = _oracle_proposals_on_gpu(P, t, Ls, reals, envs, beta, S, 3, 0)
+    acc = t.mh_step(g_props, state, seed=3).cpu().numpy()
+    assert acc[:, 0].all()
+    for n, L in enumerate(Ls):
+        start = (np.zeros((L, L), np.uint8), np.inf, 0.0)
+        (o_sig, o_lq, o_E), o_acc, o_lr, o_u = mh.chain(start, o_props[n], beta, 3, 0, n)
+        assert o_acc[0] == 1
+        near = np.abs(np.log(o_u) - o_lr) < 1e-12
+        assert np.array_equal(acc[n][~near], o_acc[~near])
+        assert state.logq.cpu().numpy()[n] == o_lq
 
 
 @pytest.mark.parametrize("prec", ["fp32", "mixed"])
@@ -154,30 +196,44 @@ def test_fp32_log_z_and_draw_audit(P, Ls, chi, beta, kind, prec):
     """float32 mode against the float64 oracle.
 
     |d log Z| / L^2 <= 1e-6 (cases whose cut gaps are wide); energies exact;
-    teacher-forced audit: every draw agrees with the oracle's float64
-    conditional unless the uniform lies within 2e-3 of its probability.
+    teacher-forced audit on the oracle's proposals: at every site the GPU's
+    float32 conditional takes the oracle's decision under the same uniform
+    unless the uniform lies within 2e-3 of the oracle's probability; the free
+    running GPU proposals equal the oracle's up to such a draw.
     log q: float32 rounding of the cache alone already moves log q by ~1e-3
     at beta = 2 (test_fp32_storage_bound in test_precision_model.py), so the
     bound here is 1e-2, not the float64 1e-9.
     """
     S = 64
-    t, reals, lz, props, (lg, _, _), st, flags = _run(P, Ls, chi, beta, prec, kind, S, diag=True)
+    t, reals, lz, props, _, st, flags = _run(P, Ls, chi, beta, prec, kind, S)
     assert st == 0
     envs = parity.oracle_envs(reals, beta, chi, t.cutoff)   # the same truncation rule
-    spins = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
-    lq = props.logq.cpu().numpy()
+    o_props = [sampler.propose(rows, Jh, Jv, beta, S, 42, 0, n)
+               for n, ((Jh, Jv), rows) in enumerate(zip(reals, envs))]
+    spins_in = torch.from_numpy(np.concatenate([o[0].reshape(-1) for o in o_props])).cuda()
+    g_lq, g_E, g_lg = t.score_logits(spins_in, S)
+    g_lq, g_E, g_lg = g_lq.cpu().numpy(), g_E.cpu().numpy(), g_lg.cpu().numpy()
+    g_sig = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
+    off = 0
     for n, (L, (Jh, Jv), rows) in enumerate(zip(Ls, reals, envs)):
+        o_sig, o_lq, o_E, o_lg = o_props[n]
         assert min(g for r in rows for g in r.cut_gap) > 1e-2
         assert abs(lz[n] - bmps.log_z(rows)) / (L * L) < 1e-6
-        o_lq, o_E, o_lg = sampler.score(rows, Jh, Jv, beta, spins[n])
-        np.testing.assert_array_equal(props.E.cpu().numpy()[n], o_E)
-        assert np.abs(lq[n] - o_lq).max() < 1e-2
+        np.testing.assert_array_equal(g_E[n], o_E)
+        assert np.abs(g_lq[n] - o_lq).max() < 1e-2
         u = philox.spin_uniforms(L, np.arange(S, dtype=np.uint64), n, 42)
         p = sampler.sigmoid(o_lg)
-        want = (u < p).astype(np.uint8)
-        got = spins[n].reshape(S, -1)
+        lg = g_lg[off:off + S * L * L].reshape(S, L * L)
+        off += S * L * L
+        gpu_decision = (u < sampler.sigmoid(lg)).astype(np.uint8)
         band = np.abs(u - p) < 2e-3
-        assert np.array_equal(got[~band], want[~band])
+        assert np.array_equal(gpu_decision[~band], o_sig.reshape(S, -1)[~band])
+        # free running: equal until a draw inside the band
+        for k in range(S):
+            a, b = g_sig[n][k].reshape(-1), o_sig[k].reshape(-1)
+            if not np.array_equal(a, b):
+                i = int(np.argmax(a != b))
+                assert band[k, i], (n, k, i)
 
 
 def test_bad_couplings_flagged(P):
