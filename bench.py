@@ -361,6 +361,15 @@ def run_ours(args, wl):
         else:
             peak, peak_src = FP64_NOMINAL_GFLOPS, "nominal float64 rate (recipe table, not measured)"
         proposals = wl.n_real * S * args.steps
+        # DRAM bytes per launch of this kernel: the float32, chi = 64 instantiation was
+        # captured on 8 realizations at L = 128 (131072 site-rows, 2.206 GB read + written,
+        # profiles/env_build_fp32_L128.md); traffic grows with the site-rows written
+        site_rows = sum(L * L for L in wl.Ls)
+        if args.prec == "fp32" and t.plan_ch == 64 and not ckpt:
+            traffic = 2.206e9 / 131072 * site_rows
+            traffic_src = "ncu capture at L=128 x 8 realizations, scaled by site-rows"
+        else:
+            traffic, traffic_src = None, "no capture of this instantiation"
         cpu = None
         if world == 1 and args.cpu_baseline:
             t_real, rows_done, _ = oracle_sample(wl, seconds=args.ref_seconds)
@@ -395,7 +404,8 @@ def run_ours(args, wl):
             "roofline": {"kernel": "env_build_kernel (boundary-MPS build)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
                          "frac": achieved / peak, "peak_source": peak_src,
-                         "traffic": None,
+                         "traffic": traffic,
+                         "traffic_source": traffic_src,
                          "algorithmic_flops_per_launch": flops_env},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_acc_all / e2e_s_all, "unit": "accepted/s",

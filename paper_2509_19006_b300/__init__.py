@@ -181,6 +181,7 @@ class TNMC:
         self.sum_L2 = sum(L * L for L in self.Ls)
         self.cutoff = float(cutoff) if cutoff > 0 else self.DEFAULT_CUTOFF.get(self.prec, 1e-6)
         self.ckpt_every = int(ckpt_every)
+        self.plan_ch = next((c for c in (8, 16, 32, 64) if self.chi <= c), 0)   # kernel instantiation
         self._cfg, self._cfg_keep = _cfg(self.Ls, chi, beta, self.prec, max_samples, self.cutoff,
                                          self.ckpt_every)
         nbytes = ctypes.c_size_t(0)

@@ -104,4 +104,6 @@ def config(name: str) -> Workload:
         return Workload("L128_chi64_beta3_n8_S256", [128] * 8, 3.0, 64, 256)
     if name == "L40x1":
         return Workload("L40_chi64_beta3_n1_S64", [40], 3.0, 64, 64)
+    if name == "gauss128x8":   # 8 realizations of the Gaussian workload (profiler captures)
+        return Workload("gauss_L128_chi8_beta2_n8", [128] * 8, 2.0, 8, 256, kind="gauss")
     raise KeyError(name)
