@@ -157,12 +157,6 @@ __device__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int 
   }
 }
 
-// Round-robin (circle method) schedule: in round k, seat s holds player
-// 0 (s = 0) or 1 + (s - 1 + k) mod (P - 1); seats p and P-1-p play.
-__device__ __forceinline__ int seat_player(int seat, int k, int P) {
-  return seat == 0 ? 0 : 1 + (seat - 1 + k) % (P - 1);
-}
-
 // Jacobi rotation (c, s, t = s / c) that orthogonalises two rows with squared
 // norms alpha, beta and inner product gamma. The angle only needs about float32
 // accuracy (an inexact angle leaves a small residual for the next sweep); what
@@ -178,46 +172,53 @@ __device__ __forceinline__ void rotation_params(T al, T be, T ga, T &cs, T &sn, 
 template <>
 __device__ __forceinline__ void rotation_params<float>(float al, float be, float ga, float &cs,
                                                        float &sn, float &t) {
-  const float zeta = (be - al) / (2.f * ga);
+  const float num = be - al;
+  const float zeta = __fdividef(num, 2.f * ga);
   const float az = fabsf(zeta);
-  t = az > 1e15f ? 0.5f / zeta : copysignf(1.f, zeta) / (az + sqrtf(1.f + zeta * zeta));
-  if (zeta == 0.f) t = 1.f;
-  cs = rsqrtf(1.f + t * t);
-  sn = cs * t;
-}
-__device__ __forceinline__ double rcp_approx(double x) {
-  double y;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  return y;
-}
-__device__ __forceinline__ double rsqrt_approx(double x) {
-  double y;
-  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  return y;
+  float tf;
+  if (az > 1e15f) {
+    tf = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.f);
+    tf = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
+  }
+  if (num == 0.f) tf = 1.f;
+  cs = rsqrtf(fmaf(tf, tf, 1.f));
+  sn = cs * tf;
+  t = tf;
 }
 template <>
 __device__ __forceinline__ void rotation_params<double>(double al, double be, double ga, double &cs,
                                                         double &sn, double &t) {
-  const double num = be - al;
-  const double zeta = num * rcp_approx(2.0 * ga);
-  const double az = fabs(zeta);
-  double tt;
-  if (az > 1e15) tt = 0.5 * rcp_approx(zeta);
-  else {
-    const double q = fma(zeta, zeta, 1.0);
-    tt = copysign(rcp_approx(az + q * rsqrt_approx(q)), zeta);
+  // zeta = num / den in float32: both are brought into float range by the
+  // exponent of the larger one, read from its bit pattern (a power-of-two
+  // scaling is exact); float64 arithmetic is left only for that scaling and
+  // the orthogonality rescale below
+  const double num = be - al, den = 2.0 * ga;
+  const double big = fmax(fabs(num), fabs(den));
+  int e = ((__double2hiint(big) >> 20) & 0x7ff) - 1023;
+  e = max(min(e, 1022), -1022);
+  const double sc = __hiloint2double((1023 - e) << 20, 0);   // 2^-e
+  const float fn = (float)(num * sc), fd = (float)(den * sc);
+  const float zeta = __fdividef(fn, fd);
+  const float az = fabsf(zeta);
+  float tf;
+  if (az > 1e15f) {
+    tf = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.f);
+    tf = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
   }
-  if (num == 0.0) tt = 1.0;
-  const double c0 = rsqrt_approx(fma(tt, tt, 1.0));
-  const double s0 = c0 * tt;
-  // c^2 + s^2 = 1 to working precision: rescale by 1/sqrt(1+d) ~ 1 - d/2 + 3d^2/8;
-  // the approximate rsqrt is good to ~1e-6, so |d| < 4e-6 and the series'
-  // remainder 5|d|^3/16 stays below 2e-17
+  if (fn == 0.f) tf = 1.f;
+  const float c0f = rsqrtf(fmaf(tf, tf, 1.f));
+  const double c0 = c0f, s0 = (double)(c0f * tf);
+  // c^2 + s^2 = 1 to working precision: rescale by 1/sqrt(1+d) ~ 1 - d/2 + 3d^2/8
+  // (|d| ~ 1e-7 from the float32 pair; the series' remainder 5|d|^3/16 < 1e-20)
   const double d = fma(c0, c0, fma(s0, s0, -1.0));
   const double r = fma(d, fma(0.375, d, -0.5), 1.0);
   cs = c0 * r;
   sn = s0 * r;
-  t = tt;
+  t = tf;
 }
 
 // One-sided (Hestenes) Jacobi on the rows of the nr x nc row-major matrix B
@@ -272,13 +273,20 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
   }
   half_barrier(half);
   for (int sweep = 0; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
+    // Round-robin (circle method) schedule: in round k, seat s holds player 0
+    // (s = 0) or 1 + (s - 1 + k) mod (P - 1), and seats p and P-1-p play. The
+    // positions (s - 1 + k) mod (P - 1) of this lane's two seats advance by one
+    // every round.
+    int pa = gi - 1, pb = P - 2 - gi;
     for (int k = 0; k < P - 1; ++k) {
       if (warp_active) {
         const bool full = (k == 0);
         int i = -1, j = -1, solo = -1;
         if (gi < npairs) {
-          i = seat_player(gi, k, P);
-          j = seat_player(P - 1 - gi, k, P);
+          i = gi == 0 ? 0 : 1 + pa;
+          j = 1 + pb;
+          pa = (pa + 1 == P - 1) ? 0 : pa + 1;
+          pb = (pb + 1 == P - 1) ? 0 : pb + 1;
           if (i >= nr || j >= nr) {
             // odd row count: this row sits the round out, but its norm is still refreshed
             solo = (full && i < nr) ? perm[i] : ((full && j < nr) ? perm[j] : -1);
@@ -297,7 +305,15 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
               al += av * av; be += bv * bv; ga += av * bv;
             }
           } else {
-            for (int x = gl; x < nc; x += TPP) ga += a[x] * b[x];
+            // two accumulators: halves the dependent multiply-add chain
+            T g0 = 0, g1 = 0;
+            int x = gl;
+            for (; x + TPP < nc; x += 2 * TPP) {
+              g0 += a[x] * b[x];
+              g1 += a[x + TPP] * b[x + TPP];
+            }
+            if (x < nc) g0 += a[x] * b[x];
+            ga = g0 + g1;
           }
         } else if (solo >= 0) {
           const T *a = B + int64_t(solo) * ldb;
