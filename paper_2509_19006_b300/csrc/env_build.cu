@@ -70,6 +70,44 @@ __device__ __forceinline__ void half_barrier(int half) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + half), "r"(256) : "memory");
 }
 
+// ---- two-CTA clusters (float64 build with at most 74 realizations): the
+// second CTA of a cluster runs the Jacobi SVD of parity sector 1 on its own
+// SM, its rows shipped through distributed shared memory.
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.aligned;\nbarrier.cluster.wait.aligned;" ::: "memory");
+}
+// address of the same shared variable in CTA `rank` of this cluster (generic)
+template <typename T>
+__device__ __forceinline__ T *peer_ptr(T *p, unsigned rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
+  return reinterpret_cast<T *>(out);
+}
+__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+__device__ __forceinline__ void store_release_cluster(unsigned *p, unsigned v) {
+  asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned load_acquire_cluster(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Wait until *p == want, at most `budget` cycles; false if the wait ran out.
+__device__ __forceinline__ bool wait_flag(const unsigned *p, unsigned want, long long budget) {
+  const long long t0 = clock64();
+  while (load_acquire_cluster(p) != want) {
+    if (clock64() - t0 > budget) return false;
+    __nanosleep(200);
+  }
+  return true;
+}
+constexpr long long CLUSTER_WAIT_CYCLES = 40000000000ll;   // ~20 s at 2 GHz
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -235,15 +273,18 @@ __device__ __forceinline__ void rotation_params<double>(double al, double be, do
 // norms, refreshed in the first round of every sweep).
 // Only the warps that own a pair this round execute arithmetic: with float64
 // on B300 every idle warp's instruction costs the whole SM issue slots.
-template <typename T, int TPP>
+// NT threads take part: 256 (one half of the CTA, ht = its thread index, synchronised by
+// the half's named barrier) or 512 (the whole CTA, ht = threadIdx.x, __syncthreads).
+template <typename T, int TPP, int NT = 256>
 __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int ht,
                            volatile int *lastrot, T *nrm2, const int *perm) {
+  static_assert(NT == 256 || NT == 512, "a half or the whole CTA");
   if (nr <= 1) return 0;  // uniform over the half
   const int P = nr + (nr & 1);
   const int npairs = P / 2;
   // the second half's active pairs start on the third scheduler partition, so
   // both halves' float64 work spreads over all four partitions
-  const int vt = half ? ((ht + 192) & 255) : ht;
+  const int vt = (NT == 512 || !half) ? ht : ((ht + 192) & 255);
   const int gi = vt / TPP, gl = vt % TPP;
   const bool warp_active = (vt & ~31) < npairs * TPP;
   // The computed cosine of a pair carries a rounding error ~ sqrt(nc) eps, so
@@ -253,12 +294,15 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
   // rows orthogonal closer to the rounding floor); float64 at 8 sqrt(nc) eps
   const T tf = sizeof(T) == 4 ? T(4) : T(64);
   const T tol2 = tf * Num<T>::eps() * Num<T>::eps() * T(nc > 4 ? nc : 4);
-  for (int i = ht; i < nr; i += 256) {
+  auto sync = [half]() {
+    if (NT == 512) __syncthreads(); else half_barrier(half);
+  };
+  for (int i = ht; i < nr; i += NT) {
     T s2 = 0;
     for (int x = 0; x < nc; ++x) { const T v = B[int64_t(i) * ldb + x]; s2 += v * v; }
     nrm2[i] = s2;
   }
-  half_barrier(half);
+  sync();
   // Rows whose norm is below eps x the largest are rounding noise: rotating
   // them only stirs noise (a rotation with a larger row leaves their norm of
   // the same size, and they never pass any cutoff), so they are left alone.
@@ -271,7 +315,7 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
     for (int i = 0; i < nr; ++i) mx = nrm2[i] > mx ? nrm2[i] : mx;
     floor2 = sizeof(T) == 8 ? mx * Num<T>::eps() * Num<T>::eps() : T(0);
   }
-  half_barrier(half);
+  sync();
   for (int sweep = 0; sweep < JACOBI_MAX_SWEEPS; ++sweep) {
     // Round-robin (circle method) schedule: in round k, seat s holds player 0
     // (s = 0) or 1 + (s - 1 + k) mod (P - 1), and seats p and P-1-p play. The
@@ -352,7 +396,7 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
           else if (full) { nrm2[i] = al <= floor2 ? kNoise : al; nrm2[j] = be <= floor2 ? kNoise : be; }
         }
       }
-      half_barrier(half);
+      sync();
     }
     if (*lastrot < sweep) return sweep + 1;  // no rotation in this sweep (all threads agree)
   }
@@ -369,7 +413,7 @@ __device__ __forceinline__ double log_cosh(double x) {
 }
 
 // TC: arithmetic of the build (and the carry between rows); TS: cache storage.
-template <typename TC, typename TS, int CH>
+template <typename TC, typename TS, int CH, bool SPLIT>
 __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   using P = EnvPlan<TC, TS, CH>;
   constexpr int LDA = P::LDA, LDT = P::LDT;
@@ -384,6 +428,10 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   __shared__ TC Bnrm[2 * CH];        // squared row norms cached by the Jacobi sweeps
   __shared__ TC sh_tv, sh_th, sh_smax;
   __shared__ long long sh_clk[5];    // cycles per phase of the current row (diagnostics)
+  // cluster mode: task (rank 1 reads) and result (rank 0 reads) mailboxes
+  __shared__ unsigned sh_task_seq, sh_done_seq, sh_sent;
+  __shared__ int sh_task[4];         // rows, columns, stop, first row of sector 1 in the owner
+  __shared__ int sh_done_nsw, sh_helper_dead;
   long long t_mark = 0;
 
   const int tid = threadIdx.x, half = tid >> 8, ht = tid & 255;
@@ -392,7 +440,8 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   const int64_t chi2 = int64_t(chi) * chi;
   const double beta = lay.beta;
 
-  unsigned char *slot = (unsigned char *)lay.env_scratch + int64_t(blockIdx.x) * lay.env_slot_bytes;
+  const int slot_idx = SPLIT ? int(blockIdx.x >> 1) : int(blockIdx.x);
+  unsigned char *slot = (unsigned char *)lay.env_scratch + int64_t(slot_idx) * lay.env_slot_bytes;
   TC *Qstore = (TC *)slot;
   int4 *info = (int4 *)(slot + P::q_bytes(lay.L_max));
   TC *carry = (TC *)(slot + P::q_bytes(lay.L_max) + P::info_bytes(lay.L_max));
@@ -406,12 +455,63 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   TC *tau = W + P::oTau;
   TC *sn = W + P::oSn;
 
+  static_assert(!SPLIT || P::in_smem, "cluster mode keeps Theta in shared memory");
+  if (SPLIT) {
+    if (tid == 0) { sh_task_seq = 0; sh_done_seq = 0; sh_sent = 0; sh_helper_dead = 0; }
+    cluster_sync_all();   // both CTAs are running (and initialised) before any remote access
+    if (cluster_rank() == 1) {
+      // ---- helper: run sector 1's Jacobi for the other CTA until told to stop
+      TC *peer_Th = peer_ptr(Th, 0u);
+      __shared__ int sh_go;
+      for (unsigned task_no = 1;; ++task_no) {
+        if (tid == 0) {
+          const bool ok = wait_flag(&sh_task_seq, task_no, CLUSTER_WAIT_CYCLES);
+          sh_go = ok && sh_task[2] == 0;
+          if (!ok) set_flag(lay.flags, 0, FLAG_TIMEOUT);
+        }
+        __syncthreads();
+        fence_cluster();
+        if (!sh_go) break;
+        const int rows = sh_task[0], N = sh_task[1], row0 = sh_task[3];
+        if (tid == 0) sh_lastrot[0] = -1;
+        const int nsw = tid < 256
+                            ? jacobi_rows<TC, 8>(Th, rows, N, rows, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src)
+                            : 0;
+        __syncthreads();
+        // the rotated rows back into the owner's Theta, sector 1 at its row row0
+        for (int e = tid; e < rows * (N + rows); e += ENV_THREADS) {
+          const int r = e / (N + rows), x = e % (N + rows);
+          peer_Th[int64_t(row0 + r) * LDT + x] = Th[int64_t(r) * LDT + x];
+        }
+        fence_cluster();
+        __syncthreads();
+        if (tid == 0) {
+          *peer_ptr(&sh_done_nsw, 0u) = nsw;
+          fence_cluster();
+          store_release_cluster(peer_ptr(&sh_done_seq, 0u), task_no);
+        }
+      }
+      cluster_sync_all();
+      return;
+    }
+  }
+
   for (;;) {
     if (tid == 0) sh_n = atomicAdd(lay.counter, 1);
     __syncthreads();
     const int idx = sh_n;
     __syncthreads();
-    if (idx >= lay.n_real) break;
+    if (idx >= lay.n_real) {
+      if (SPLIT) {
+        if (tid == 0) {
+          *peer_ptr(&sh_task[2], 1u) = 1;   // stop
+          fence_cluster();
+          store_release_cluster(peer_ptr(&sh_task_seq, 1u), sh_sent + 1);
+        }
+        cluster_sync_all();
+      }
+      break;
+    }
     const int n = lay.order[idx];
     const RealInfo ri = lay.reals[n];
     const int L = ri.L;
@@ -643,15 +743,61 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         }
         __syncthreads();
         if (tid == 0) { const long long t1 = clock64(); sh_clk[2] += t1 - t_mark; t_mark = t1; }
-        {
+        if (SPLIT && !sh_helper_dead) {
+          // cluster mode: sector 1 (two rows or more) goes to the helper CTA, sector 0 is
+          // rotated here (each sector has an SM to itself)
+          const bool send = k1 >= 2;
+          if (send) {
+            TC *hTh = peer_ptr(Th, 1u);
+            int *hsrc = peer_ptr(sh_src, 1u);
+            for (int e = tid; e < k1 * (N + k1); e += ENV_THREADS) {
+              const int r = e / (N + k1), x = e % (N + k1);
+              hTh[int64_t(r) * LDT + x] = Th[int64_t(k0 + r) * LDT + x];
+            }
+            for (int r = tid; r < k1; r += ENV_THREADS) hsrc[r] = sh_src[k0 + r];
+            fence_cluster();
+            __syncthreads();
+            if (tid == 0) {
+              int *h_task = peer_ptr(sh_task, 1u);
+              h_task[0] = k1;
+              h_task[1] = N;
+              h_task[2] = 0;
+              h_task[3] = k0;   // the row where sector 1 starts here
+              fence_cluster();
+              store_release_cluster(peer_ptr(&sh_task_seq, 1u), ++sh_sent);
+            }
+          }
+          // 8 lanes per row pair on one half (measured: faster than 4 lanes, and than
+          // 16 lanes over the whole CTA, whose barrier costs more than its warps gain)
+          const int nsw0 = half == 0
+                               ? jacobi_rows<TC, 8>(Th, k0, N, k0, LDT, 0, ht, &sh_lastrot[0], Bnrm, sh_src)
+                               : 0;
+          if (tid == 0) {
+            if (nsw0 > 0) { sh_sweeps += nsw0; sh_svds += 1; }
+            if (send) {
+              if (wait_flag(&sh_done_seq, sh_sent, CLUSTER_WAIT_CYCLES)) {
+                if (sh_done_nsw > 0) { sh_sweeps += sh_done_nsw; sh_svds += 1; }
+              } else {
+                set_flag(lay.flags, n, FLAG_TIMEOUT);
+                sh_helper_dead = 1;
+              }
+            }
+          }
+          __syncthreads();
+          if (send && sh_helper_dead) {   // the helper gave up: rotate sector 1 here
+            const int nsw1 = jacobi_rows<TC, 16, 512>(Th + int64_t(k0) * LDT, k1, N, k1, LDT, 0, tid,
+                                                      &sh_lastrot[1], Bnrm + CH, sh_src + k0);
+            if (tid == 0 && nsw1 > 0) { sh_sweeps += nsw1; sh_svds += 1; }
+          }
+        } else {
           const int rows = half ? k1 : k0;
-          int nsw;
           TC *Bq = Th + int64_t(half ? k0 : 0) * LDT;
-          nsw = jacobi_rows<TC, 4>(Bq, rows, N, rows, LDT, half, ht, &sh_lastrot[half],
-                                   Bnrm + (half ? CH : 0), sh_src + (half ? k0 : 0));
+          const int nsw = jacobi_rows<TC, 4>(Bq, rows, N, rows, LDT, half, ht, &sh_lastrot[half],
+                                             Bnrm + (half ? CH : 0), sh_src + (half ? k0 : 0));
           if (ht == 0 && nsw > 0) { atomicAdd(&sh_sweeps, nsw); atomicAdd(&sh_svds, 1); }
         }
         __syncthreads();
+        if (SPLIT) fence_cluster();   // the helper's rows, acquired by one thread, for all
         if (tid == 0) { const long long t1 = clock64(); sh_clk[3] += t1 - t_mark; t_mark = t1; }
         // singular values = row norms
         for (int i = tid; i < m; i += ENV_THREADS) {
@@ -793,34 +939,64 @@ int64_t env_slot_bytes(int mode, int CH, int L_max, int chi) {
   return env_slot_bytes_ts<double, float>(CH, L_max, chi);
 }
 
-template <typename TC, typename TS, int CH>
+template <typename TC, typename TS, int CH, bool SPLIT>
 static cudaError_t launch_env_t(const Layout &lay, cudaStream_t st) {
   using P = EnvPlan<TC, TS, CH>;
   const int smem = P::in_smem ? int(P::bytes) : 0;
-  cudaError_t e = cudaFuncSetAttribute(env_build_kernel<TC, TS, CH>,
+  cudaError_t e = cudaFuncSetAttribute(env_build_kernel<TC, TS, CH, SPLIT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(lay.counter, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  env_build_kernel<TC, TS, CH><<<lay.env_slots, ENV_THREADS, smem, st>>>(lay);
+  if (!SPLIT) {
+    env_build_kernel<TC, TS, CH, false><<<lay.env_slots, ENV_THREADS, smem, st>>>(lay);
+    return cudaGetLastError();
+  }
+  // pairs of CTAs: the second of each pair serves sector 1's Jacobi SVDs
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * lay.env_slots);
+  cfg.blockDim = dim3(ENV_THREADS);
+  cfg.dynamicSmemBytes = size_t(smem);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, env_build_kernel<TC, TS, CH, true>, lay);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 template <typename TC, typename TS>
-static cudaError_t launch_env_ts(const Layout &lay, int CH, cudaStream_t st) {
+static cudaError_t launch_env_ts(const Layout &lay, int CH, bool split, cudaStream_t st) {
+  if (split) {
+    switch (CH) {
+      case 8: return launch_env_t<TC, TS, 8, true>(lay, st);
+      case 16: return launch_env_t<TC, TS, 16, true>(lay, st);
+      case 32: return launch_env_t<TC, TS, 32, true>(lay, st);
+      case 64: return launch_env_t<TC, TS, 64, true>(lay, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (CH) {
-    case 8: return launch_env_t<TC, TS, 8>(lay, st);
-    case 16: return launch_env_t<TC, TS, 16>(lay, st);
-    case 32: return launch_env_t<TC, TS, 32>(lay, st);
-    case 64: return launch_env_t<TC, TS, 64>(lay, st);
+    case 8: return launch_env_t<TC, TS, 8, false>(lay, st);
+    case 16: return launch_env_t<TC, TS, 16, false>(lay, st);
+    case 32: return launch_env_t<TC, TS, 32, false>(lay, st);
+    case 64: return launch_env_t<TC, TS, 64, false>(lay, st);
   }
   return cudaErrorInvalidValue;
 }
 
+// The float64 build runs as CTA pairs (one SM per parity sector's Jacobi) when
+// the pairs of all realizations fit on the GPU at once (148 SMs: 74 pairs);
+// float64 rotations are bound by one SM's float64 rate.
 cudaError_t launch_env_build(const Layout &lay, int mode, int CH, cudaStream_t st) {
-  if (mode == 0) return launch_env_ts<double, double>(lay, CH, st);
-  if (mode == 1) return launch_env_ts<float, float>(lay, CH, st);
-  return launch_env_ts<double, float>(lay, CH, st);
+  if (mode == 0) return launch_env_ts<double, double>(lay, CH, lay.env_slots <= 74, st);
+  if (mode == 1) return launch_env_ts<float, float>(lay, CH, false, st);
+  return launch_env_ts<double, float>(lay, CH, false, st);
 }
 
 }  // namespace tnmc
