@@ -39,10 +39,10 @@ def _net(P, seed, w3_scale=1.0):
     theta = learned.pack(W1, rng.standard_normal(64) * 0.5, W2, rng.standard_normal(64) * 0.5,
                          w3_scale * rng.standard_normal(64) * 0.3, 0.2)
     net = P.MLP(seed=seed)
-    net.load(theta.astype(np.float32))
-    torch.cuda.synchronize()
-    theta_bf = net.bf16.float().cpu().numpy().astype(np.float64)
-    return net, theta_bf
+    theta32 = theta.astype(np.float32)
+    net.load(theta32)                       # the GPU packs its own bfloat16 copy
+    net.host_theta = theta32
+    return net, learned.to_bf16(theta32)    # the oracle rounds the same float32 values
 
 
 def _examples(seed, n):
@@ -55,8 +55,8 @@ def _examples(seed, n):
 
 def test_pack_is_round_to_nearest_even(P):
     net, theta_bf = _net(P, 11)
-    master = net.params.cpu().numpy().astype(np.float64)
-    np.testing.assert_array_equal(theta_bf, learned.to_bf16(master))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(net.bf16.float().cpu().numpy().astype(np.float64), theta_bf)
 
 
 def test_forward_matches_oracle(P):
@@ -108,7 +108,7 @@ def test_adam_matches_oracle(P):
     g = (rng.standard_normal(P.MLP_PARAMS) * 1e-2).astype(np.float32)
     g[5313:] = 0
     g[np.arange(1024).reshape(64, 16)[:, 7:].reshape(-1)] = 0
-    th0 = net.params.cpu().numpy().astype(np.float64)
+    th0 = net.host_theta.astype(np.float64)
     m0 = np.zeros(P.MLP_PARAMS)
     v0 = np.zeros(P.MLP_PARAMS)
     th, m, v = th0, m0, v0
@@ -118,7 +118,8 @@ def test_adam_matches_oracle(P):
         th, m, v = learned.adam(th, (g * step).astype(np.float64), m, v, step, 1e-3)
     torch.cuda.synchronize()
     np.testing.assert_allclose(net.params.cpu().numpy(), th, rtol=1e-6, atol=1e-7)
-    np.testing.assert_array_equal(net.bf16.float().cpu().numpy(), learned.to_bf16(net.params.cpu().numpy()))
+    # the bfloat16 copy is the master rounded to nearest even (torch's conversion as the reference)
+    assert torch.equal(net.bf16, net.params.to(torch.bfloat16))
 
 
 def test_features_match_oracle(P):
