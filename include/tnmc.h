@@ -311,6 +311,17 @@ tnmc_status tnmc_propose_static(tnmc_handle *h, int32_t S, uint64_t seed, uint64
 /* Bytes of the fixed device array used by tnmc_propose_static. */
 size_t tnmc_propose_static_limit(void);
 
+/* Budget, in SM clock cycles, of every bounded device wait of this handle's
+ * later calls (0 = the default, about 20 s). The float64 build of at most 74
+ * realizations runs as pairs of CTAs that hand parity sector 1's Jacobi SVDs
+ * to each other through distributed shared memory; each hand-off waits on a
+ * flag for at most this budget. A wait that runs out sets TNMC_FLAG_TIMEOUT
+ * (read by tnmc_get_device_status as TNMC_ERR_TIMEOUT), the owning CTA then
+ * does the work itself, and the launch ends normally. Failure-detection tests
+ * set a tiny budget to make the waits run out (the paper has no counterpart).
+ * Errors: TNMC_ERR_ARG. */
+tnmc_status tnmc_set_wait_budget(tnmc_handle *h, int64_t cycles);
+
 /* Copy the per-realization device flags (TNMC_FLAG_*) to h_flags [n_real],
  * after synchronising the stream; clears them when clear != 0.
  * Returns TNMC_OK, or TNMC_ERR_NUMERIC / TNMC_ERR_TIMEOUT if any flag of

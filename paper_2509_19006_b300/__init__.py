@@ -28,7 +28,7 @@ EXPORTED = [
     "tnmc_mh_step", "tnmc_set_diagnostics", "tnmc_get_device_status", "tnmc_layout_info",
     "tnmc_propose_static", "tnmc_propose_static_limit", "tnmc_set_correction",
     "tnmc_mlp_features", "tnmc_mlp_scratch_floats", "tnmc_mlp_grad", "tnmc_mlp_adam",
-    "tnmc_mlp_pack", "tnmc_mlp_forward", "tnmc_mh_init_empty",
+    "tnmc_mlp_pack", "tnmc_mlp_forward", "tnmc_mh_init_empty", "tnmc_set_wait_budget",
 ]
 
 # learned proposal correction: parameter vector layout (include/tnmc.h)
@@ -81,6 +81,7 @@ def load_library():
         "tnmc_score": ([vp, i32, vp, vp, vp], i32),
         "tnmc_mh_init": ([vp, u64, vp, vp, vp], i32),
         "tnmc_mh_init_empty": ([vp, vp, vp, vp], i32),
+        "tnmc_set_wait_budget": ([vp, ctypes.c_int64], i32),
         "tnmc_mh_step": ([vp, i32, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "tnmc_set_diagnostics": ([vp, vp, vp, vp], i32),
         "tnmc_get_device_status": ([vp, vp, i32], i32),
@@ -326,6 +327,10 @@ class TNMC:
         _check(self.lib.tnmc_mlp_features(self.h, int(S), _ptr(spins), _ptr(logits), _ptr(feat)),
                "tnmc_mlp_features")
         return feat
+
+    def set_wait_budget(self, cycles: int):
+        """Budget of the bounded device waits in SM cycles (0 = default, ~20 s)."""
+        _check(self.lib.tnmc_set_wait_budget(self.h, int(cycles)), "tnmc_set_wait_budget")
 
     def device_status(self, clear: bool = True):
         """(status code, per-realization flags) after synchronising the stream."""

@@ -240,6 +240,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
   lay.ckpt_every = cfg->ckpt_every;
   lay.seg_begin = -1;
   lay.seg_end = 0;
+  lay.wait_cycles = 0;
   lay.bonds = reinterpret_cast<int2 *>(ws + p.off_bonds);
   lay.lam = reinterpret_cast<double *>(ws + p.off_lam);
   lay.flags = reinterpret_cast<int32_t *>(ws + p.off_flags);
@@ -299,6 +300,12 @@ tnmc_status tnmc_mlp_features(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
                  cudaSuccess
              ? TNMC_OK
              : TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_set_wait_budget(tnmc_handle *h, int64_t cycles) {
+  if (!h || cycles < 0) return TNMC_ERR_ARG;
+  h->lay.wait_cycles = cycles;
+  return TNMC_OK;
 }
 
 tnmc_status tnmc_build_envs(tnmc_handle *h, const float *d_J) {

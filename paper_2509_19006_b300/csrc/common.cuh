@@ -47,6 +47,7 @@ struct Layout {
   int32_t ckpt_every;        // K: 0 = every row cached; else checkpoint rows + one segment
   int32_t seg_begin;         // rows [seg_begin, seg_end) of this launch; seg_begin < 0 = all rows
   int32_t seg_end;
+  int64_t wait_cycles;       // budget of a bounded device wait (0: the kernel's default)
   int2 *bonds;               // [sum L (L+1)]: (even, odd) dimension of bond b of row r
   double *lam;               // [sum L]: log scale lambda_r of row r
   int32_t *flags;            // [n_real]: FLAG_* bits

@@ -456,6 +456,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   TC *sn = W + P::oSn;
 
   static_assert(!SPLIT || P::in_smem, "cluster mode keeps Theta in shared memory");
+  const long long wait_budget = lay.wait_cycles > 0 ? lay.wait_cycles : CLUSTER_WAIT_CYCLES;
   if (SPLIT) {
     if (tid == 0) { sh_task_seq = 0; sh_done_seq = 0; sh_sent = 0; sh_helper_dead = 0; }
     cluster_sync_all();   // both CTAs are running (and initialised) before any remote access
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
       __shared__ int sh_go;
       for (unsigned task_no = 1;; ++task_no) {
         if (tid == 0) {
-          const bool ok = wait_flag(&sh_task_seq, task_no, CLUSTER_WAIT_CYCLES);
+          const bool ok = wait_flag(&sh_task_seq, task_no, wait_budget);
           sh_go = ok && sh_task[2] == 0;
           if (!ok) set_flag(lay.flags, 0, FLAG_TIMEOUT);
         }
@@ -775,7 +776,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           if (tid == 0) {
             if (nsw0 > 0) { sh_sweeps += nsw0; sh_svds += 1; }
             if (send) {
-              if (wait_flag(&sh_done_seq, sh_sent, CLUSTER_WAIT_CYCLES)) {
+              if (wait_flag(&sh_done_seq, sh_sent, wait_budget)) {
                 if (sh_done_nsw > 0) { sh_sweeps += sh_done_nsw; sh_svds += 1; }
               } else {
                 set_flag(lay.flags, n, FLAG_TIMEOUT);

@@ -61,3 +61,27 @@ def test_checkpoint_argument_checks(P):
     with pytest.raises(P.TnmcError) as e:
         P.TNMC([8], 4, 1.0, "mixed", max_samples=4, ckpt_every=4)
     assert e.value.status == 7
+
+
+def test_cluster_wait_that_runs_out_reports_timeout(P):
+    """The float64 build hands parity sector 1 to a partner CTA; with a tiny wait budget the
+    hand-offs run out: the call returns, the status is TNMC_ERR_TIMEOUT, the owner did the
+    work itself, and at the default budget the same handle builds correctly again."""
+    Ls, chi, beta = [10, 8], 8, 1.5
+    reals = parity.realizations(Ls, "pmj")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    ref = P.TNMC(Ls, chi, beta, "fp64", max_samples=4)
+    ref.build_envs(J)
+    lz_ref = ref.log_z().cpu().numpy()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=4)
+    t.set_wait_budget(1)
+    t.build_envs(J)
+    t.log_z()
+    st, flags = t.device_status()
+    assert st == 5 and (flags & 4).any(), (st, flags)      # TNMC_ERR_TIMEOUT, TNMC_FLAG_TIMEOUT
+    t.set_wait_budget(0)
+    t.build_envs(J)
+    lz = t.log_z().cpu().numpy()
+    st, flags = t.device_status()
+    assert st == 0 and not flags.any()
+    np.testing.assert_allclose(lz, lz_ref, rtol=1e-12)
