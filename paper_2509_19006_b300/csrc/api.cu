@@ -37,7 +37,7 @@ using namespace tnmc;
 namespace {
 
 constexpr int kMaxL = 4096;
-constexpr int kEnvSlots = 148;   // concurrent realizations of the environment build (SM count)
+constexpr int kEnvSlots = 148;   // workspace slots of the environment build: at most one per SM of a B300
 
 struct Plan {
   int CH = 0;

@@ -992,10 +992,16 @@ static cudaError_t launch_env_ts(const Layout &lay, int CH, bool split, cudaStre
 }
 
 // The float64 build runs as CTA pairs (one SM per parity sector's Jacobi) when
-// the pairs of all realizations fit on the GPU at once (148 SMs: 74 pairs);
-// float64 rotations are bound by one SM's float64 rate.
+// the pairs of all realizations fit on the GPU at once (2 x realizations <= SMs;
+// 74 pairs on a 148-SM B300).
 cudaError_t launch_env_build(const Layout &lay, int mode, int CH, cudaStream_t st) {
-  if (mode == 0) return launch_env_ts<double, double>(lay, CH, lay.env_slots <= 74, st);
+  if (mode == 0) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    return launch_env_ts<double, double>(lay, CH, 2 * lay.env_slots <= sms, st);
+  }
   if (mode == 1) return launch_env_ts<float, float>(lay, CH, false, st);
   return launch_env_ts<double, float>(lay, CH, false, st);
 }

@@ -301,3 +301,30 @@ def test_beta3_float64_truncation_matches_oracle(P, prec):
         # rho_s = |l M R|, see test_precision_model.py); float64 keeps them
         w = -(props.logq.cpu().numpy()[0] + beta * props.E.cpu().numpy()[0])
         assert w.std() < 1e-6
+
+
+def test_fp64_single_cta_build_with_many_realizations(P):
+    """More realizations than CTA pairs fit on the GPU: the float64 build runs one CTA per
+    realization (both parity sectors on one SM). log Z of every realization and the
+    proposals of a few match the oracle as in the paired build."""
+    rng = np.random.default_rng(3)
+    Ls = [int(x) for x in rng.integers(2, 7, size=160)]
+    chi, beta, S = 4, 1.2, 24
+    reals = parity.realizations(Ls, "gauss")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    t.build_envs(J)
+    lz = t.log_z().cpu().numpy()
+    props = t.propose(S, 42, 0)
+    torch.cuda.synchronize()
+    st, flags = t.device_status()
+    assert st == 0 and not flags.any()
+    envs = parity.oracle_envs(reals, beta, chi)
+    for n in range(len(Ls)):
+        assert abs(lz[n] - bmps.log_z(envs[n])) < 1e-10 * max(1.0, abs(lz[n])), n
+    sig = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
+    lq, E = props.logq.cpu().numpy(), props.E.cpu().numpy()
+    for n in (0, 1, 77, 159):
+        Jh, Jv = reals[n]
+        n_eq, n_bd = parity.compare_proposals(envs[n], Jh, Jv, beta, 42, 0, n, sig[n], lq[n], E[n])
+        assert n_eq + n_bd == S and n_bd <= 1
