@@ -422,6 +422,82 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def run_sweep(args):
+    """Acceptance against system size, and the time of the paper's L=1024 configuration.
+
+    For each (beta, chi) the paper quotes (Sec. 4: P_acc ~ 0.37 at L = 1024, beta = 1,
+    chi = 8; comparable at beta = 1.5, chi = 16), 16 +-J realizations per L: the
+    environments, a first round of S proposals that starts the chains (tnmc_mh_init_empty),
+    and a measured round; one JSON line per (beta, chi, L). Then 64 realizations at
+    L = 1024, beta = 1, chi = 8: one step (environments, S proposals, MH) timed with CUDA
+    events, and the time it implies for 10^3 accepted samples in each of 10^3 realizations
+    (the paper's single-GPU figure is 3.3 h, on its own hardware).
+    """
+    import torch
+    import paper_2509_19006_b300 as P
+    from workloads import Workload
+    S = 256
+    sizes = [int(x) for x in args.sweep_sizes.split(",")]
+    for beta, chi in [(0.66, 4), (1.0, 8), (1.5, 16)]:
+        for L in sizes:
+            wl = Workload(f"sweep_L{L}", [L] * 16, beta, chi, S)
+            J = torch.from_numpy(wl.packed_J()).cuda()
+            t = P.TNMC(wl.Ls, chi, beta, args.prec, max_samples=S)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
+            t.build_envs(J)
+            ev[1].record()
+            st = t.mh_init_empty()
+            t.mh_step(t.propose(S, SAMPLING_SEED, 0), st, SAMPLING_SEED)
+            n0 = st.n_accept.clone()
+            t.mh_step(t.propose(S, SAMPLING_SEED, S), st, SAMPLING_SEED)
+            ev[2].record()
+            torch.cuda.synchronize()
+            acc = (st.n_accept - n0).cpu().numpy() / S
+            print(json.dumps({"sweep": "acceptance", "beta": beta, "chi": chi, "L": L, "precision": args.prec,
+                              "realizations": 16, "samples": S, "acceptance_mean": float(acc.mean()),
+                              "acceptance_sem": float(acc.std() / np.sqrt(acc.size)),
+                              "env_build_s": ev[0].elapsed_time(ev[1]) / 1e3,
+                              "status": int(t.device_status()[0])}), flush=True)
+            del t, J
+            torch.cuda.empty_cache()
+    # the paper's configuration at L = 1024
+    L, beta, chi, n_real = 1024, 1.0, 8, 64
+    wl = Workload("paper_L1024_beta1_chi8", [L] * n_real, beta, chi, S)
+    J = torch.from_numpy(wl.packed_J()).cuda()
+    t = P.TNMC(wl.Ls, chi, beta, args.prec, max_samples=S)
+    st = t.mh_init_empty()
+    t.build_envs(J)
+    t.mh_step(t.propose(S, SAMPLING_SEED, 0), st, SAMPLING_SEED)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    n0 = st.n_accept.clone()
+    ev[0].record()
+    t.build_envs(J)
+    ev[1].record()
+    props = t.propose(S, SAMPLING_SEED, S)
+    ev[2].record()
+    t.mh_step(props, st, SAMPLING_SEED)
+    ev[3].record()
+    torch.cuda.synchronize()
+    acc = float((st.n_accept - n0).sum().item()) / (S * n_real)
+    env_s, prop_s, mh_s = (ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3,
+                           ev[2].elapsed_time(ev[3]) / 1e3)
+    step_s = env_s + prop_s + mh_s
+    # 10^3 realizations x 10^3 accepted samples: environments once per realization,
+    # proposals in rounds of S per realization until 10^3 are accepted
+    waves = int(np.ceil(1000 / min(n_real, 148)))
+    hours = (waves * env_s + 1000 * 1000 / acc / (S * n_real) * (prop_s + mh_s)) / 3600
+    print(json.dumps({"sweep": "paper_configuration", "L": L, "beta": beta, "chi": chi,
+                      "precision": args.prec, "realizations": n_real, "samples": S,
+                      "acceptance": acc, "env_build_s": env_s, "proposals_s": prop_s, "mh_s": mh_s,
+                      "accepted_per_s": acc * S * n_real / step_s,
+                      "projected_hours_1000x1000": hours,
+                      "projected_hours_1000x1000_proposals":
+                          (waves * env_s + 1000 * 1000 / (S * n_real) * (prop_s + mh_s)) / 3600,
+                      "paper_hours_1000x1000": 3.3, "status": int(t.device_status()[0])}), flush=True)
+
+
 def run_env_once(args, wl):
     """Build the environments of the workload once (a target for profiler captures)."""
     import torch
@@ -456,11 +532,16 @@ def main():
                     help="train the learned correction (setup) and time the corrected steps")
     ap.add_argument("--teacher-chi", type=int, default=32)
     ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--sweep", action="store_true",
+                    help="acceptance against L at the paper's (beta, chi), and its L=1024 configuration")
+    ap.add_argument("--sweep-sizes", default="16,32,64,128,256,512,1024")
     ap.add_argument("--env-once", action="store_true",
                     help="build the environments once and exit (for profiler captures)")
     args = ap.parse_args()
     wl = config(args.workload)
-    if args.env_once:
+    if args.sweep:
+        run_sweep(args)
+    elif args.env_once:
         run_env_once(args, wl)
     elif args.impl == "reference":
         run_reference(args, wl)
