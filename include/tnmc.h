@@ -95,7 +95,8 @@ typedef struct {
                             score and mh_init then rebuild each K-row segment from the
                             checkpoint below it before sampling it (top segment first),
                             about one more environment build per call. Results are the same
-                            bits as with 0. Not available with TNMC_MIXED (TNMC_ERR_UNSUPPORTED). */
+                            bits as with 0. With TNMC_MIXED the checkpoint rows are also kept
+                            in float64 (the precision the build carries between rows). */
 } tnmc_config;
 
 typedef struct tnmc_handle tnmc_handle;

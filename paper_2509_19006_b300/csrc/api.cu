@@ -44,7 +44,8 @@ struct Plan {
   int64_t sum_L2 = 0, sum_L = 0, sum_bonds = 0, sum_cache = 0;   // sum_cache: chi x chi matrices
   int L_max = 0;
   int64_t off_reals, off_order, off_flags, off_counter, off_jr, off_jd, off_cache, off_bonds,
-      off_lam, off_env, off_samp, total;
+      off_lam, off_env, off_samp, off_ckpt64, total;
+  int64_t sum_ckpt = 0;   // chi x chi matrices of float64 checkpoint rows (MIXED + checkpoints)
   int64_t cache_bytes, env_bytes, samp_bytes, env_slot;
   int env_slots;
 };
@@ -64,9 +65,6 @@ tnmc_status check_cfg(const tnmc_config *cfg) {
   if (cfg->ckpt_every < 0 || cfg->ckpt_every == 1) return TNMC_ERR_ARG;
   if (cfg->prec == TNMC_TF32 || cfg->prec == TNMC_BF16) return TNMC_ERR_UNSUPPORTED;
   if (cfg->prec != TNMC_FP64 && cfg->prec != TNMC_FP32 && cfg->prec != TNMC_MIXED) return TNMC_ERR_ARG;
-  // MIXED carries rows between builds in float64 but caches float32: a checkpoint
-  // would have to hold the float64 row; not provided
-  if (cfg->ckpt_every > 0 && cfg->prec == TNMC_MIXED) return TNMC_ERR_UNSUPPORTED;
   for (int n = 0; n < cfg->n_real; ++n)
     if (cfg->L[n] < 1 || cfg->L[n] > kMaxL) return TNMC_ERR_ARG;
   return TNMC_OK;
@@ -88,6 +86,8 @@ Plan make_plan(const tnmc_config *cfg) {
     p.sum_L += L;
     p.sum_bonds += L * (L + 1);
     p.sum_cache += cache_rows(int(L), cfg->ckpt_every) * L;
+    if (cfg->ckpt_every > 0 && cfg->prec == TNMC_MIXED)
+      p.sum_ckpt += int64_t((L + cfg->ckpt_every - 1) / cfg->ckpt_every) * L;
     p.L_max = std::max<int>(p.L_max, int(L));
   }
   int64_t o = 0;
@@ -108,6 +108,8 @@ Plan make_plan(const tnmc_config *cfg) {
   p.off_env = take(p.env_bytes);
   p.samp_bytes = int64_t(cfg->max_samples) * p.sum_L * p.CH * esz;
   p.off_samp = take(p.samp_bytes);
+  // MIXED carries the build between rows in float64: its checkpoints keep that row
+  p.off_ckpt64 = take(p.sum_ckpt * int64_t(cfg->chi) * cfg->chi * 8);
   p.total = o;
   return p;
 }
@@ -207,7 +209,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
 
   // per-realization table and the longest-first order
   std::vector<RealInfo> reals(cfg->n_real);
-  int64_t so = 0, bo = 0, ro = 0, co = 0;
+  int64_t so = 0, bo = 0, ro = 0, co = 0, ko = 0;
   for (int n = 0; n < cfg->n_real; ++n) {
     const int64_t L = cfg->L[n];
     reals[n].L = int32_t(L);
@@ -217,8 +219,10 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
     reals[n].row_off = ro;
     reals[n].line_off = ro;
     reals[n].cache_off = co;
+    reals[n].ckpt_off = ko;
     so += L * L; bo += L * (L + 1); ro += L;
     co += cache_rows(int(L), cfg->ckpt_every) * L;
+    if (cfg->ckpt_every > 0 && cfg->prec == TNMC_MIXED) ko += int64_t((L + cfg->ckpt_every - 1) / cfg->ckpt_every) * L;
   }
   std::vector<int32_t> order(cfg->n_real);
   std::iota(order.begin(), order.end(), 0);
@@ -241,6 +245,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
   lay.seg_begin = -1;
   lay.seg_end = 0;
   lay.wait_cycles = 0;
+  lay.ckpt64 = p.sum_ckpt > 0 ? reinterpret_cast<double *>(ws + p.off_ckpt64) : nullptr;
   lay.bonds = reinterpret_cast<int2 *>(ws + p.off_bonds);
   lay.lam = reinterpret_cast<double *>(ws + p.off_lam);
   lay.flags = reinterpret_cast<int32_t *>(ws + p.off_flags);

@@ -29,6 +29,7 @@ struct RealInfo {
   int64_t row_off;    // sum_{m<n} L_m: rows before it
   int64_t line_off;   // sum_{m<n} L_m: sampler scratch lines (per sample) before it
   int64_t cache_off;  // first chi x chi matrix of this realization in the cache
+  int64_t ckpt_off;   // first chi x chi matrix of its float64 checkpoint rows (MIXED + checkpoints)
 };
 
 // Device-side view of the workspace; passed by value to every kernel.
@@ -48,6 +49,7 @@ struct Layout {
   int32_t seg_begin;         // rows [seg_begin, seg_end) of this launch; seg_begin < 0 = all rows
   int32_t seg_end;
   int64_t wait_cycles;       // budget of a bounded device wait (0: the kernel's default)
+  double *ckpt64;            // MIXED with checkpoints: the checkpoint rows in float64, or null
   int2 *bonds;               // [sum L (L+1)]: (even, odd) dimension of bond b of row r
   double *lam;               // [sum L]: log scale lambda_r of row r
   int32_t *flags;            // [n_real]: FLAG_* bits

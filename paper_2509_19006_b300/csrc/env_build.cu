@@ -529,6 +529,13 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
     if (lay.flags[n] & FLAG_BAD_J) continue;  // uniform: read by all threads after the barrier
 
     if (tid == 0) sh_lam = (r_hi < L - 1) ? lay.lam[ri.row_off + r_hi + 1] : 0.0;
+    if (P::split_carry && K > 0 && lay.seg_begin >= 0 && r_hi < L - 1) {
+      // a segment resumes the float64 build from the float64 copy of the checkpoint below it
+      const double *src = lay.ckpt64 + (ri.ckpt_off + int64_t((r_hi + 1) / K) * L) * chi2;
+      TC *dstc = carry + int64_t((r_hi + 1) & 1) * L * chi2;
+      for (int64_t e = tid; e < int64_t(L) * chi2; e += ENV_THREADS) dstc[e] = TC(src[e]);
+      __syncthreads();
+    }
     for (int r = r_hi; r >= r_lo; --r) {
       const bool trivial_prev = (r == L - 1);
       // the previous row in the build's own precision
@@ -913,6 +920,12 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         curE = ne; curO = no;
         __syncthreads();
         if (tid == 0) { const long long t1 = clock64(); sh_clk[4] += t1 - t_mark; t_mark = t1; }
+      }
+      // MIXED with checkpoints: keep the float64 row of every checkpoint (full build only;
+      // the next row reads this buffer and writes the other one)
+      if (P::split_carry && K > 0 && lay.seg_begin < 0 && r % K == 0) {
+        double *ck = lay.ckpt64 + (ri.ckpt_off + int64_t(r / K) * L) * chi2;
+        for (int64_t e = tid; e < int64_t(L) * chi2; e += ENV_THREADS) ck[e] = double(ccur[e]);
       }
     }
   }

@@ -19,7 +19,7 @@ def P():
     return P
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
 @pytest.mark.parametrize("K", [2, 3, 5])
 def test_checkpointed_equals_full_cache(P, prec, K):
     Ls, chi, beta, S = [9, 6, 12], 4, 1.5, 70
@@ -27,7 +27,8 @@ def test_checkpointed_equals_full_cache(P, prec, K):
     J = torch.from_numpy(parity.packed_J(reals)).cuda()
     full = P.TNMC(Ls, chi, beta, prec, max_samples=S)
     ck = P.TNMC(Ls, chi, beta, prec, max_samples=S, ckpt_every=K)
-    assert ck.ws_bytes < full.ws_bytes or K >= 5
+    # (MIXED also keeps float64 checkpoint rows, which outweigh the saving at these tiny sizes)
+    assert ck.ws_bytes < full.ws_bytes or K >= 5 or prec == "mixed"
     for t in (full, ck):
         t.build_envs(J)
     assert torch.equal(full.log_z(), ck.log_z())
@@ -58,9 +59,6 @@ def test_checkpointed_equals_full_cache(P, prec, K):
 def test_checkpoint_argument_checks(P):
     with pytest.raises(P.TnmcError):
         P.TNMC([8], 4, 1.0, "fp32", max_samples=4, ckpt_every=1)
-    with pytest.raises(P.TnmcError) as e:
-        P.TNMC([8], 4, 1.0, "mixed", max_samples=4, ckpt_every=4)
-    assert e.value.status == 7
 
 
 def test_cluster_wait_that_runs_out_reports_timeout(P):
