@@ -22,7 +22,6 @@
 // and SVD splits into two independent problems of half the size, which the
 // two halves of the CTA (256 threads each) solve concurrently.
 #include "common.cuh"
-#include <cstdio>
 
 namespace tnmc {
 
