@@ -498,6 +498,63 @@ def run_sweep(args):
                       "paper_hours_1000x1000": 3.3, "status": int(t.device_status()[0])}), flush=True)
 
 
+def run_serial_vs_batch(args):
+    """The gain of batching (the paper's R1, Eq. 11, measured with this code on one GPU).
+
+    Serial: one realization, its environments, then proposals one at a time (S = 1 per
+    call), each followed by its MH step. Batched: n realizations at once and S proposals per
+    call. Both at L, beta = 1, chi = 8 (the paper's speed-up setting, at a size that runs in
+    seconds). Reported: time per proposal in each mode, the environment time per
+    realization, and the ratio of the two times for n x S proposals.
+    """
+    import torch
+    import paper_2509_19006_b300 as P
+    from workloads import Workload
+    L, beta, chi, n_real, S, n_serial = args.rs_L, 1.0, 8, 64, 256, 32
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # serial
+    wl1 = Workload("serial", [L], beta, chi, 1)
+    J1 = torch.from_numpy(wl1.packed_J()).cuda()
+    t1 = P.TNMC(wl1.Ls, chi, beta, args.prec, max_samples=1)
+    t1.build_envs(J1)
+    st1 = t1.mh_init_empty()
+    torch.cuda.synchronize()
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record()
+    t1.build_envs(J1)
+    e1.record()
+    for k in range(n_serial):
+        t1.mh_step(t1.propose(1, SAMPLING_SEED, k), st1, SAMPLING_SEED)
+    e2.record()
+    torch.cuda.synchronize()
+    env1 = e0.elapsed_time(e1) / 1e3
+    per_prop_serial = e1.elapsed_time(e2) / 1e3 / n_serial
+    # batched
+    wl = Workload("batched", [L] * n_real, beta, chi, S)
+    J = torch.from_numpy(wl.packed_J()).cuda()
+    t = P.TNMC(wl.Ls, chi, beta, args.prec, max_samples=S)
+    t.build_envs(J)
+    st = t.mh_init_empty()
+    torch.cuda.synchronize()
+    f0, f1, f2 = ev(), ev(), ev()
+    f0.record()
+    t.build_envs(J)
+    f1.record()
+    t.mh_step(t.propose(S, SAMPLING_SEED, 0), st, SAMPLING_SEED)
+    f2.record()
+    torch.cuda.synchronize()
+    env_b = f0.elapsed_time(f1) / 1e3
+    per_prop_batch = f1.elapsed_time(f2) / 1e3 / (n_real * S)
+    t_serial = n_real * (env1 + S * per_prop_serial)
+    t_batch = env_b + n_real * S * per_prop_batch
+    print(json.dumps({"serial_vs_batch": True, "L": L, "beta": beta, "chi": chi, "precision": args.prec,
+                      "realizations": n_real, "samples": S,
+                      "serial": {"env_build_s": env1, "s_per_proposal": per_prop_serial},
+                      "batched": {"env_build_s": env_b, "s_per_proposal": per_prop_batch},
+                      "time_serial_s": t_serial, "time_batched_s": t_batch,
+                      "ratio": t_serial / t_batch}), flush=True)
+
+
 def run_env_once(args, wl):
     """Build the environments of the workload once (a target for profiler captures)."""
     import torch
@@ -535,12 +592,17 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="acceptance against L at the paper's (beta, chi), and its L=1024 configuration")
     ap.add_argument("--sweep-sizes", default="16,32,64,128,256,512,1024")
+    ap.add_argument("--serial-vs-batch", action="store_true",
+                    help="time serial (one realization, one proposal at a time) against batched")
+    ap.add_argument("--rs-L", type=int, default=256)
     ap.add_argument("--env-once", action="store_true",
                     help="build the environments once and exit (for profiler captures)")
     args = ap.parse_args()
     wl = config(args.workload)
     if args.sweep:
         run_sweep(args)
+    elif args.serial_vs_batch:
+        run_serial_vs_batch(args)
     elif args.env_once:
         run_env_once(args, wl)
     elif args.impl == "reference":

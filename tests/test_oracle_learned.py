@@ -261,3 +261,45 @@ def test_mh_with_corrected_proposal_samples_boltzmann():
     chi2 = np.sum((obs - exp_) ** 2 / exp_)
     dof = obs.size - 1
     assert chi2 < dof + 6 * np.sqrt(2 * dof), (chi2, dof)
+
+
+# ---------------------------------------------------------------- importance-sampling observables
+def test_observables_exact_proposal_gives_exact_log_z_and_unit_weights():
+    """On a forest q = P exactly, so every weight equals Z: the IS log Z is the closed form."""
+    from oracle import observables as ob
+    L, beta = 5, 0.9
+    Jh, Jv = draw_bonds(L, 80, "pmj")
+    Jv = np.zeros_like(Jv)                      # independent rows: a forest
+    rows = bmps.build_envs(Jh, Jv, beta, 2)
+    sig, lq, E, _ = sampler.propose(rows, Jh, Jv, beta, 64, 42, 0, 0)
+    v = ob.observables(sig, lq, E, beta)
+    lz_exact = L * L * np.log(2.0) + np.sum(np.log(np.cosh(beta * Jh.astype(np.float64))))
+    assert abs(v[0] - lz_exact) < 1e-10 and abs(v[1] - 64) < 1e-9
+
+
+def test_observables_match_brute_force_averages():
+    """With chi exact (L=3), the IS averages of E/N and q^2 converge to the enumerated ones."""
+    from oracle import observables as ob
+    L, beta, S = 3, 0.7, 20000
+    Jh, Jv = draw_bonds(L, 81, "gauss")
+    rows = bmps.build_envs(Jh, Jv, beta, 1)     # a poor chi: the weights do the correcting
+    sig, lq, E, _ = sampler.propose(rows, Jh, Jv, beta, S, 42, 0, 0)
+    v = ob.observables(sig, lq, E, beta)
+    cfgs, E_all, logp, lz = exact.brute_force(Jh, Jv, beta)
+    p = np.exp(logp)
+    cfg = np.asarray(cfgs).reshape(len(p), -1).astype(np.float64) * 2 - 1
+    qab = cfg @ cfg.T / 9.0
+    q2_exact = p @ (qab ** 2) @ p
+    assert abs(v[2] - p @ E_all / 9.0) < 0.02
+    assert abs(v[3] - q2_exact) < 0.02
+    # the IS log Z within five of its standard errors: var(w)/mean(w)^2 = S/ESS - 1
+    err = np.sqrt((S / v[1] - 1.0) / S)
+    assert abs(v[0] - lz) < 5 * err, (v[0], lz, err)
+
+
+def test_binder_ratio_of_a_fully_ordered_sample_is_one():
+    from oracle import observables as ob
+    sig = np.ones((8, 4, 4), np.uint8)
+    v = ob.observables(sig, np.zeros(8), np.zeros(8), 1.0)
+    assert v[3] == 1.0 and v[4] == 1.0 and v[5] == 1.0
+    assert abs(ob.nishimori_beta(0.1) - 0.5 * np.log(9.0)) < 1e-15
