@@ -498,6 +498,44 @@ def run_sweep(args):
                       "paper_hours_1000x1000": 3.3, "status": int(t.device_status()[0])}), flush=True)
 
 
+def run_nishimori(args):
+    """Random-bond Ising model on the Nishimori line (SURVEY.md's next step after the
+    acceptance curve): +-J bonds antiferromagnetic with probability p, beta with
+    exp(-2 beta) = p / (1 - p). Per (p, L), 32 realizations, S proposals each: the
+    importance-sampling observables (tnmc_observables) averaged over disorder, with the
+    exact identity [<E>] = -N_B (1 - 2p) as a check, and the IS log Z against the
+    boundary-MPS log Z of the same environments.
+    """
+    import torch
+    import paper_2509_19006_b300 as P
+    from workloads import Workload
+    S, n_real, chi = 256, 32, 16
+    for p in (0.05, 0.1):
+        beta = 0.5 * float(np.log((1.0 - p) / p))
+        for L in (16, 32, 64):
+            wl = Workload(f"nishimori_p{p}_L{L}", [L] * n_real, beta, chi, S, p=p, base_seed=9000)
+            J = torch.from_numpy(wl.packed_J()).cuda()
+            t = P.TNMC(wl.Ls, chi, beta, args.prec, max_samples=S)
+            t.build_envs(J)
+            lz = t.log_z().cpu().numpy()
+            obs = t.observables(t.propose(S, SAMPLING_SEED, 0)).cpu().numpy()
+            nb = 2 * L * (L - 1)
+            e_bond = obs[:, 2] * L * L / nb
+            sem = lambda x: float(np.std(x) / np.sqrt(x.size))
+            print(json.dumps({"nishimori": True, "p": p, "beta": beta, "L": L, "chi": chi,
+                              "precision": args.prec, "realizations": n_real, "samples": S,
+                              "energy_per_bond": float(e_bond.mean()), "energy_per_bond_sem": sem(e_bond),
+                              "energy_per_bond_exact": -(1 - 2 * p),
+                              "q2": float(obs[:, 3].mean()), "q2_sem": sem(obs[:, 3]),
+                              "binder": float(obs[:, 5].mean()), "binder_sem": sem(obs[:, 5]),
+                              "ess_mean": float(obs[:, 1].mean()),
+                              "is_minus_bmps_log_z": float((obs[:, 0] - lz).mean()),
+                              "is_minus_bmps_log_z_sem": sem(obs[:, 0] - lz),
+                              "status": int(t.device_status()[0])}), flush=True)
+            del t, J
+            torch.cuda.empty_cache()
+
+
 def run_serial_vs_batch(args):
     """The gain of batching (the paper's R1, Eq. 11, measured with this code on one GPU).
 
@@ -595,6 +633,8 @@ def main():
     ap.add_argument("--serial-vs-batch", action="store_true",
                     help="time serial (one realization, one proposal at a time) against batched")
     ap.add_argument("--rs-L", type=int, default=256)
+    ap.add_argument("--nishimori", action="store_true",
+                    help="random-bond Ising model on the Nishimori line: observables and the energy identity")
     ap.add_argument("--env-once", action="store_true",
                     help="build the environments once and exit (for profiler captures)")
     args = ap.parse_args()
@@ -603,6 +643,8 @@ def main():
         run_sweep(args)
     elif args.serial_vs_batch:
         run_serial_vs_batch(args)
+    elif args.nishimori:
+        run_nishimori(args)
     elif args.env_once:
         run_env_once(args, wl)
     elif args.impl == "reference":

@@ -162,6 +162,19 @@ tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
 tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
                          double *d_state_logq, double *d_state_E);
 
+/* Importance-sampling observables of S proposals per realization (the layouts of
+ * tnmc_propose). With weights w_k = exp(-beta E_k - log q_k) (Eq. 1, Eq. 9; the
+ * ratio of Eq. 10), d_out: float64 [n_real][6] receives per realization
+ *   log mean_k w_k (an estimate of log Z), the effective sample size
+ *   (sum w)^2 / sum w^2, the energy per spin sum w E / (N sum w), and, over the
+ *   proposal pairs (0,1), (2,3), ... weighted by w_a w_b, the overlap moments
+ *   <q^2>, <q^4> of q_ab = (1/N) sum_i s_i^a s_i^b and the Binder ratio
+ *   (3 - <q^4>/<q^2>^2) / 2 (NaN when S < 2); N = L_n^2.
+ * Weights are formed in the log domain, shifted by their maximum; every sum runs
+ * in a fixed order. Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+tnmc_status tnmc_observables(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
+                             const double *d_logq, const double *d_E, double *d_out);
+
 /* A chain state with no configuration yet: spins 0, E = 0 and log q = +inf,
  * so that the first proposal of the next tnmc_mh_step has log r = +inf and is
  * accepted: the chain then starts at a draw of q (the paper has no

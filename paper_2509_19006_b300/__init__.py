@@ -29,6 +29,7 @@ EXPORTED = [
     "tnmc_propose_static", "tnmc_propose_static_limit", "tnmc_set_correction",
     "tnmc_mlp_features", "tnmc_mlp_scratch_floats", "tnmc_mlp_grad", "tnmc_mlp_adam",
     "tnmc_mlp_pack", "tnmc_mlp_forward", "tnmc_mh_init_empty", "tnmc_set_wait_budget",
+    "tnmc_observables",
 ]
 
 # learned proposal correction: parameter vector layout (include/tnmc.h)
@@ -82,6 +83,7 @@ def load_library():
         "tnmc_mh_init": ([vp, u64, vp, vp, vp], i32),
         "tnmc_mh_init_empty": ([vp, vp, vp, vp], i32),
         "tnmc_set_wait_budget": ([vp, ctypes.c_int64], i32),
+        "tnmc_observables": ([vp, i32, vp, vp, vp, vp], i32),
         "tnmc_mh_step": ([vp, i32, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "tnmc_set_diagnostics": ([vp, vp, vp, vp], i32),
         "tnmc_get_device_status": ([vp, vp, i32], i32),
@@ -327,6 +329,14 @@ class TNMC:
         _check(self.lib.tnmc_mlp_features(self.h, int(S), _ptr(spins), _ptr(logits), _ptr(feat)),
                "tnmc_mlp_features")
         return feat
+
+    def observables(self, props: Proposals):
+        """Per realization (n_real, 6): IS log Z, ESS, E/N, <q^2>, <q^4>, Binder ratio."""
+        t = self.torch
+        out = t.empty((self.n_real, 6), dtype=t.float64, device=self.device)
+        _check(self.lib.tnmc_observables(self.h, int(props.S), _ptr(props.spins), _ptr(props.logq),
+                                         _ptr(props.E), _ptr(out)), "tnmc_observables")
+        return out
 
     def set_wait_budget(self, cycles: int):
         """Budget of the bounded device waits in SM cycles (0 = default, ~20 s)."""

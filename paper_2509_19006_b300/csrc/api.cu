@@ -15,6 +15,8 @@ cudaError_t launch_env_build(const Layout &lay, int mode, int CH, cudaStream_t s
 cudaError_t launch_log_z(const Layout &lay, int prec, double *logz, cudaStream_t st);
 cudaError_t launch_init_state(const Layout &lay, uint64_t seed, uint8_t *spins, cudaStream_t st);
 cudaError_t launch_empty_state(const Layout &lay, double *logq, double *E, cudaStream_t st);
+cudaError_t launch_observables(const Layout &lay, int S, const uint8_t *spins, const double *logq,
+                               const double *E, double *out, cudaStream_t st);
 cudaError_t launch_mh(const Layout &lay, int S, uint64_t seed, uint64_t base, const uint8_t *ps,
                       const double *pl, const double *pe, uint8_t *ss, double *sl, double *se,
                       uint8_t *acc, int64_t *nacc, cudaStream_t st);
@@ -386,6 +388,14 @@ tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
                           h->stream);
     });
   return e == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_observables(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
+                             const double *d_logq, const double *d_E, double *d_out) {
+  if (!h || !d_spins || !d_logq || !d_E || !d_out || S < 1) return TNMC_ERR_ARG;
+  return launch_observables(h->lay, S, d_spins, d_logq, d_E, d_out, h->stream) == cudaSuccess
+             ? TNMC_OK
+             : TNMC_ERR_CUDA;
 }
 
 tnmc_status tnmc_mh_init_empty(tnmc_handle *h, uint8_t *d_state_spins, double *d_state_logq,

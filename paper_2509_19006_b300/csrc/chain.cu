@@ -154,6 +154,89 @@ cudaError_t launch_log_z(const Layout &lay, int prec, double *logz, cudaStream_t
   return cudaGetLastError();
 }
 
+// Importance-sampling observables of each realization's S proposals, with weights
+// w_k = exp(-beta E_k - log q_k) (Eq. 1, Eq. 9; the ratio of Eq. 10): log mean w,
+// the effective sample size (sum w)^2 / sum w^2, <E>/N, and over the proposal
+// pairs (2k, 2k+1) with pair weights w_a w_b the overlap moments <q^2>, <q^4> of
+// q_ab = (1/N) sum_i s_i^a s_i^b and the Binder ratio (3 - <q^4>/<q^2>^2) / 2.
+// One CTA per realization; every sum in a fixed order.
+constexpr int OBS_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < OBS_THREADS / 32; ++w) t += red[w];
+  return t;
+}
+
+__global__ void observables_kernel(Layout lay, int S, const uint8_t *spins, const double *logq,
+                                   const double *E, double *out) {
+  __shared__ double red[OBS_THREADS / 32];
+  __shared__ double sh_m;
+  const int n = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const RealInfo ri = lay.reals[n];
+  const int64_t N = int64_t(ri.L) * ri.L;
+  const double beta = lay.beta;
+  const double *lq = logq + int64_t(n) * S, *en = E + int64_t(n) * S;
+  // the largest log weight (log-domain shift)
+  double m = -INFINITY;
+  for (int k = tid; k < S; k += OBS_THREADS) m = fmax(m, -beta * en[k] - lq[k]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) red[warp] = m;
+  __syncthreads();
+  if (tid == 0) {
+    double t = red[0];
+    for (int w = 1; w < OBS_THREADS / 32; ++w) t = fmax(t, red[w]);
+    sh_m = t;
+  }
+  __syncthreads();
+  m = sh_m;
+  double sw = 0.0, sw2 = 0.0, swe = 0.0;
+  for (int k = tid; k < S; k += OBS_THREADS) {
+    const double w = exp(-beta * en[k] - lq[k] - m);
+    sw += w; sw2 += w * w; swe += w * en[k];
+  }
+  sw = block_sum(sw, red);
+  sw2 = block_sum(sw2, red);
+  swe = block_sum(swe, red);
+  // replica pairs: one warp per pair counts the differing spins
+  double sp = 0.0, sq2 = 0.0, sq4 = 0.0;
+  const uint8_t *base = spins + int64_t(S) * ri.site_off;
+  for (int p = warp; p < S / 2; p += OBS_THREADS / 32) {
+    const uint8_t *a = base + int64_t(2 * p) * N, *b = a + N;
+    int64_t diff = 0;
+    for (int64_t i = lane; i < N; i += 32) diff += (a[i] != b[i]);
+    for (int o = 16; o > 0; o >>= 1) diff += __shfl_xor_sync(0xffffffffu, diff, o);
+    if (lane == 0) {
+      const double q = double(N - 2 * diff) / double(N);
+      const double wp = exp(-beta * en[2 * p] - lq[2 * p] - m) * exp(-beta * en[2 * p + 1] - lq[2 * p + 1] - m);
+      sp += wp; sq2 += wp * q * q; sq4 += wp * q * q * q * q;
+    }
+  }
+  sp = block_sum(sp, red);
+  sq2 = block_sum(sq2, red);
+  sq4 = block_sum(sq4, red);
+  if (tid == 0) {
+    double *o = out + int64_t(n) * 6;
+    o[0] = m + log(sw / double(S));
+    o[1] = sw * sw / sw2;
+    o[2] = swe / sw / double(N);
+    const double q2 = sq2 / sp, q4 = sq4 / sp;
+    o[3] = S >= 2 ? q2 : NAN;
+    o[4] = S >= 2 ? q4 : NAN;
+    o[5] = S >= 2 ? 0.5 * (3.0 - q4 / (q2 * q2)) : NAN;
+  }
+}
+
+cudaError_t launch_observables(const Layout &lay, int S, const uint8_t *spins, const double *logq,
+                               const double *E, double *out, cudaStream_t st) {
+  observables_kernel<<<lay.n_real, OBS_THREADS, 0, st>>>(lay, S, spins, logq, E, out);
+  return cudaGetLastError();
+}
+
 // A chain with no state yet: log q = +inf makes log r = +inf for the first
 // proposal, which is therefore accepted, so the chain starts at a draw of q.
 __global__ void empty_state_kernel(int n_real, double *logq, double *E) {

@@ -13,8 +13,8 @@ from workloads import draw_bonds, to_paper_layout
 BAND_FP64 = 1e-9
 
 
-def realizations(Ls, kind, base_seed=1000):
-    return [draw_bonds(L, base_seed + n, kind) for n, L in enumerate(Ls)]
+def realizations(Ls, kind, base_seed=1000, p=0.5):
+    return [draw_bonds(L, base_seed + n, kind, p) for n, L in enumerate(Ls)]
 
 
 def packed_J(reals):

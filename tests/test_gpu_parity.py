@@ -328,3 +328,38 @@ def test_fp64_single_cta_build_with_many_realizations(P):
         Jh, Jv = reals[n]
         n_eq, n_bd = parity.compare_proposals(envs[n], Jh, Jv, beta, 42, 0, n, sig[n], lq[n], E[n])
         assert n_eq + n_bd == S and n_bd <= 1
+
+
+def test_observables_match_oracle(P):
+    """tnmc_observables on the oracle's proposals (odd S, odd and even L) = the oracle's values."""
+    from oracle import observables as ob
+    Ls, chi, beta, S = [7, 6, 5], 4, 1.1, 51
+    reals = parity.realizations(Ls, "pmj", p=0.3)
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    t.build_envs(J)
+    envs = parity.oracle_envs(reals, beta, chi)
+    o_props, g_props = _oracle_proposals_on_gpu(P, t, Ls, reals, envs, beta, S, 42, 0)
+    got = t.observables(g_props).cpu().numpy()
+    for n in range(len(Ls)):
+        want = ob.observables(o_props[n][0], o_props[n][1], o_props[n][2], beta)
+        np.testing.assert_allclose(got[n], want, rtol=1e-12, atol=1e-13)
+
+
+def test_nishimori_line_energy_from_gpu_samples(P):
+    """Exact at any size: on the Nishimori line the disorder average of the thermal energy is
+    -N_B (1 - 2p). The GPU's importance-sampling energies of 64 realizations at L = 12 agree
+    within four standard errors of the disorder average."""
+    from oracle import observables as ob
+    p, L, n_real, chi, S = 0.1, 12, 64, 8, 256
+    beta = ob.nishimori_beta(p)
+    Ls = [L] * n_real
+    reals = parity.realizations(Ls, "pmj", base_seed=7000, p=p)
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    t.build_envs(J)
+    obs = t.observables(t.propose(S, 42, 0)).cpu().numpy()
+    e = obs[:, 2] * L * L                      # <E> per realization
+    nb = 2 * L * (L - 1)
+    assert obs[:, 1].min() > 0.5 * S           # the weights are nearly flat (a good q)
+    assert abs(e.mean() + nb * (1 - 2 * p)) < 4 * e.std() / np.sqrt(n_real), (e.mean(), -nb * (1 - 2 * p))

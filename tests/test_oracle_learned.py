@@ -303,3 +303,22 @@ def test_binder_ratio_of_a_fully_ordered_sample_is_one():
     v = ob.observables(sig, np.zeros(8), np.zeros(8), 1.0)
     assert v[3] == 1.0 and v[4] == 1.0 and v[5] == 1.0
     assert abs(ob.nishimori_beta(0.1) - 0.5 * np.log(9.0)) < 1e-15
+
+
+def test_nishimori_line_energy_identity_by_enumeration():
+    """On the Nishimori line exp(-2 beta) = p / (1 - p) of the +-J model, the disorder average of
+    the thermal energy is exactly -N_B (1 - 2p) (N_B bonds): enumerate all 2^12 bond
+    configurations of a 3 x 3 lattice, weight each by p^(#antiferro) (1-p)^(#ferro), and
+    average the brute-force <E>."""
+    from oracle import observables as ob
+    L, p = 3, 0.2
+    beta = ob.nishimori_beta(p)
+    nb = 2 * L * (L - 1)
+    avg = 0.0
+    for k in range(1 << nb):
+        bits = (k >> np.arange(nb)) & 1          # 1 = antiferromagnetic
+        J = np.where(bits == 1, -1.0, 1.0).astype(np.float32)
+        Jh, Jv = J[:L * (L - 1)].reshape(L, L - 1), J[L * (L - 1):].reshape(L - 1, L)
+        _, E, logp, _ = exact.brute_force(Jh, Jv, beta)
+        avg += p ** bits.sum() * (1 - p) ** (nb - bits.sum()) * float(np.exp(logp) @ E)
+    assert abs(avg - (-nb * (1 - 2 * p))) < 1e-10, avg

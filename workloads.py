@@ -70,13 +70,14 @@ class Workload:
     S: int
     kind: str = "pmj"
     base_seed: int = 1000
+    p: float = 0.5            # antiferromagnetic bond probability of the +-J model
 
     @property
     def n_real(self) -> int:
         return len(self.Ls)
 
     def realization(self, n: int):
-        return draw_bonds(self.Ls[n], self.base_seed + n, self.kind)
+        return draw_bonds(self.Ls[n], self.base_seed + n, self.kind, self.p)
 
     def packed_J(self, idx: Sequence[int] | None = None) -> np.ndarray:
         """All realizations' paper-layout couplings, concatenated: (sum L^2, 4)."""
