@@ -499,8 +499,8 @@ def run_sweep(args):
 
 
 def run_nishimori(args):
-    """Random-bond Ising model on the Nishimori line (SURVEY.md's next step after the
-    acceptance curve): +-J bonds antiferromagnetic with probability p, beta with
+    """Random-bond Ising model on the Nishimori line: +-J bonds antiferromagnetic with
+    probability p, beta with
     exp(-2 beta) = p / (1 - p). Per (p, L), 32 realizations, S proposals each: the
     importance-sampling observables (tnmc_observables) averaged over disorder, with the
     exact identity [<E>] = -N_B (1 - 2p) as a check, and the IS log Z against the

@@ -1,6 +1,6 @@
 """Importance-sampling observables of one realization from S proposals.
 
-Test infrastructure: only the tests and ``bench.py``'s CPU baseline use it.
+Test infrastructure: only the tests use it; the CUDA path never imports it.
 
 The proposals s_k are drawn from q; with weights w_k = exp(-beta E(s_k)) / q(s_k)
 (Eq. 1, Eq. 9), Z = E_q[w] (Sec. 2.3: the proposals' log q makes importance
