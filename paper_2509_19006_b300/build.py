@@ -31,16 +31,33 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):
             return LIB
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--shared", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *srcs]
+    # the sources share no device code: compile them in parallel, then link
+    obj_dir = os.path.join(PKG, "build")
+    os.makedirs(obj_dir, exist_ok=True)
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+             "-I", os.path.join(ROOT, "include")]
     if verbose_ptxas:
-        cmd.insert(1, "-Xptxas=-v")
-    res = subprocess.run(cmd, capture_output=True, text=True)
+        flags.insert(0, "-Xptxas=-v")
+    objs = [os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o") for src in srcs]
+
+    def compile_one(pair):
+        src, obj = pair
+        return subprocess.run([nvcc(), *flags, "-c", src, "-o", obj], capture_output=True, text=True)
+
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        results = list(ex.map(compile_one, zip(srcs, objs)))
+    for res in results:
+        if res.returncode != 0:
+            sys.stderr.write(res.stdout + res.stderr)
+            raise RuntimeError("nvcc failed building libtnmc.so")
+        if verbose_ptxas:
+            sys.stderr.write(res.stderr)
+    res = subprocess.run([nvcc(), *ARCH, "--shared", "-o", LIB + ".tmp", *objs],
+                         capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed building libtnmc.so")
-    if verbose_ptxas:
-        sys.stderr.write(res.stderr)
+        raise RuntimeError("nvcc failed linking libtnmc.so")
     os.replace(LIB + ".tmp", LIB)
     return LIB
 
