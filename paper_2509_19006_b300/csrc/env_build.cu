@@ -20,7 +20,14 @@
 //
 // The MPO x MPS product is block diagonal in the parity sectors, so each QR
 // and SVD splits into two independent problems of half the size, which the
-// two halves of the CTA (256 threads each) solve concurrently.
+// two halves of the CTA (256 threads each) solve concurrently. The float64
+// build of at most (SM count / 2) realizations runs as pairs of CTAs (2-CTA
+// clusters): the second CTA of a pair rotates sector 1's Jacobi SVDs on its own
+// SM, its rows exchanged through distributed shared memory.
+//
+// With checkpointed environments (Layout::ckpt_every) a launch builds either all
+// rows, keeping every K-th row, or one K-row segment from the checkpoint below
+// it (Layout::seg_begin, seg_end); see cache_slot in common.cuh.
 #include "common.cuh"
 
 namespace tnmc {

@@ -17,6 +17,12 @@
 // over the CTA's chains: each thread holds a 4 chains x 4 columns register
 // tile and streams C (staged in shared memory, double-buffered) against the
 // chains' vectors (shared memory, chain-minor).
+//
+// With the learned correction on (CORR, Layout::mlp) a 7 -> 64 -> 64 -> 1
+// network adds its output to each logit before the draw (mlp.cuh); the shifted
+// logit defines q, so log q stays exact. With checkpointed environments a launch
+// walks one segment of rows (Layout::seg_begin, seg_end) and resumes from the
+// spins, log q and energies that the segment above left.
 #include "common.cuh"
 #include "mlp.cuh"
 
