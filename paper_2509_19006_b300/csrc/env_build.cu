@@ -204,13 +204,9 @@ __device__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int 
 // Jacobi rotation (c, s, t = s / c) that orthogonalises two rows with squared
 // norms alpha, beta and inner product gamma. The angle only needs about float32
 // accuracy (an inexact angle leaves a small residual for the next sweep); what
-// must hold to working precision is c^2 + s^2 = 1, or the rotation would not
-// be orthogonal. For float64, zeta and t come from the hardware's approximate
-// float64 reciprocal and reciprocal square root, and the pair (c0, s0) is
-// rescaled by the series 1 / sqrt(n) = 1 - d/2 + 3 d^2 / 8 (d = n - 1, small),
-// which leaves c^2 + s^2 - 1 at rounding level. This keeps the float64 square
-// roots and divisions (each a long sequence on the float64 pipe) off the
-// critical path of every Jacobi round.
+// must hold to working precision is c^2 (1 + t^2) = 1, or the rotation would not
+// be orthogonal. This keeps the float64 square roots and divisions (each a long
+// sequence on the float64 pipe) off the critical path of every Jacobi round.
 template <typename T>
 __device__ __forceinline__ void rotation_params(T al, T be, T ga, T &cs, T &sn, T &t);
 template <>
@@ -231,13 +227,17 @@ __device__ __forceinline__ void rotation_params<float>(float al, float be, float
   sn = cs * tf;
   t = tf;
 }
-template <>
-__device__ __forceinline__ void rotation_params<double>(double al, double be, double ga, double &cs,
-                                                        double &sn, double &t) {
-  // zeta = num / den in float32: both are brought into float range by the
-  // exponent of the larger one, read from its bit pattern (a power-of-two
-  // scaling is exact); float64 arithmetic is left only for that scaling and
-  // the orthogonality rescale below
+
+// Float64 rows: the tangent t is the float32 value of the angle formula
+// (zeta = (beta - alpha) / (2 gamma) taken in float32 after both operands are
+// brought into float range by the exponent of the larger one, read from its bit
+// pattern; a power-of-two scaling is exact), used exactly as a float64 number.
+// c = 1 / sqrt(1 + t^2) starts from the float32 reciprocal square root c0 and is
+// corrected by the series 1 / sqrt(1 + d) = 1 - d/2 + 3 d^2 / 8 with
+// d = c0^2 (1 + t^2) - 1 (|d| ~ 1e-7; the series' remainder 5|d|^3/16 < 1e-20),
+// so that c^2 (1 + t^2) = 1 to working precision. ic = c (1 + t^2) = 1 / c.
+__device__ __forceinline__ void rotation_tangent_f64(double al, double be, double ga, double &t,
+                                                     double &c, double &ic) {
   const double num = be - al, den = 2.0 * ga;
   const double big = fmax(fabs(num), fabs(den));
   int e = ((__double2hiint(big) >> 20) & 0x7ff) - 1023;
@@ -254,15 +254,12 @@ __device__ __forceinline__ void rotation_params<double>(double al, double be, do
     tf = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
   }
   if (fn == 0.f) tf = 1.f;
-  const float c0f = rsqrtf(fmaf(tf, tf, 1.f));
-  const double c0 = c0f, s0 = (double)(c0f * tf);
-  // c^2 + s^2 = 1 to working precision: rescale by 1/sqrt(1+d) ~ 1 - d/2 + 3d^2/8
-  // (|d| ~ 1e-7 from the float32 pair; the series' remainder 5|d|^3/16 < 1e-20)
-  const double d = fma(c0, c0, fma(s0, s0, -1.0));
-  const double r = fma(d, fma(0.375, d, -0.5), 1.0);
-  cs = c0 * r;
-  sn = s0 * r;
-  t = tf;
+  const double c0 = (double)rsqrtf(fmaf(tf, tf, 1.f));
+  t = (double)tf;
+  const double q = fma(t, t, 1.0);
+  const double d = fma(c0 * c0, q, -1.0);
+  c = c0 * fma(d, fma(0.375, d, -0.5), 1.0);
+  ic = c * q;
 }
 
 // One-sided (Hestenes) Jacobi on the rows of the nr x nc row-major matrix B
@@ -277,14 +274,30 @@ __device__ __forceinline__ void rotation_params<double>(double al, double be, do
 // a <- c a - s b, b <- s a + c b, and then alpha <- alpha - t gamma,
 // beta <- beta + t gamma (Golub & Van Loan, Sec. 8.6.3; de Rijk's cached
 // norms, refreshed in the first round of every sweep).
+//
+// Float64 rows use scaled ("fast") rotations: row i is held as d_i x B_i, and
+// a rotation becomes two multiply-adds per element pair,
+//   B_a <- B_a - (t d_b / d_a) B_b,   B_b <- B_b + (t d_a / d_b) B_a,
+//   d_a <- c d_a,   d_b <- c d_b,
+// instead of four float64 operations (B300 issues about two float64
+// instructions per clock per SM, and applying rotations is most of a round).
+// The transformation of the true rows d x B is exactly the rotation (c, s).
+// Each row also keeps e_i = 1 / d_i, updated by 1/c = c (1 + t^2) and then one
+// Newton step e <- e (2 - d e), so that d_i e_i = 1 to working precision. At the
+// end of every sweep that rotated, each row is multiplied by its scale and the
+// scales reset to 1; hence d = e = 1 in the first round of every sweep, and a
+// scale never falls below cos(pi/4)^(nr-1) within a sweep.
+//
 // Only the warps that own a pair this round execute arithmetic: with float64
 // on B300 every idle warp's instruction costs the whole SM issue slots.
 // NT threads take part: 256 (one half of the CTA, ht = its thread index, synchronised by
 // the half's named barrier) or 512 (the whole CTA, ht = threadIdx.x, __syncthreads).
+// scl: 2 values per row (d_i, e_i), used by float64 rows only.
 template <typename T, int TPP, int NT = 256>
 __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int ht,
-                           volatile int *lastrot, T *nrm2, const int *perm) {
+                           volatile int *lastrot, T *nrm2, const int *perm, T *scl) {
   static_assert(NT == 256 || NT == 512, "a half or the whole CTA");
+  constexpr bool SCALED = sizeof(T) == 8;
   if (nr <= 1) return 0;  // uniform over the half
   const int P = nr + (nr & 1);
   const int npairs = P / 2;
@@ -307,6 +320,7 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
     T s2 = 0;
     for (int x = 0; x < nc; ++x) { const T v = B[int64_t(i) * ldb + x]; s2 += v * v; }
     nrm2[i] = s2;
+    if (SCALED) { scl[2 * i] = T(1); scl[2 * i + 1] = T(1); }
   }
   sync();
   // Rows whose norm is below eps x the largest are rounding noise: rotating
@@ -346,6 +360,13 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
             j = perm[j];
           }
         }
+        // row scales (float64): read by every lane of the pair before the
+        // shuffles below, written afterwards by the pair's first lane
+        T di = 1, ei = 1, dj = 1, ej = 1;
+        if (SCALED && i >= 0) {
+          di = scl[2 * i]; ei = scl[2 * i + 1];
+          dj = scl[2 * j]; ej = scl[2 * j + 1];
+        }
         T al = 0, be = 0, ga = 0;
         if (i >= 0) {
           const T *a = B + int64_t(i) * ldb, *b = B + int64_t(j) * ldb;
@@ -370,6 +391,7 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
           for (int x = gl; x < nc; x += TPP) al += a[x] * a[x];
         }
         ga = group_sum<T, TPP>(ga);
+        if (SCALED) ga *= di * dj;   // the true rows' inner product (d = 1 in a full round)
         if (full) {
           al = group_sum<T, TPP>(al);
           be = group_sum<T, TPP>(be);
@@ -386,22 +408,55 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
           const bool quiet = full ? (al <= floor2 || be <= floor2) : (al == kNoise || be == kNoise);
           // convergence test without a square root: gamma^2 > tol^2 alpha beta
           rot = !quiet && ga != T(0) && ga * ga > tol2 * (al * be);
-          if (rot) rotation_params<T>(al, be, ga, cs, sn, t);
+          if (rot) {
+            if constexpr (SCALED) rotation_tangent_f64(al, be, ga, t, cs, sn);   // sn = 1 / c
+            else rotation_params<T>(al, be, ga, cs, sn, t);
+          }
           rot = rot && fabs(t) > Num<T>::eps();
         }
         if (rot) {
           T *a = B + int64_t(i) * ldb, *b = B + int64_t(j) * ldb;
-          for (int x = gl; x < nc + nu; x += TPP) {
-            const T av = a[x], bv = b[x];
-            a[x] = cs * av - sn * bv;
-            b[x] = sn * av + cs * bv;
+          if constexpr (SCALED) {
+            const T ta = t * dj * ei, tb = t * di * ej;
+            for (int x = gl; x < nc + nu; x += TPP) {
+              const T av = a[x], bv = b[x];
+              a[x] = fma(-ta, bv, av);
+              b[x] = fma(tb, av, bv);
+            }
+          } else {
+            for (int x = gl; x < nc + nu; x += TPP) {
+              const T av = a[x], bv = b[x];
+              a[x] = cs * av - sn * bv;
+              b[x] = sn * av + cs * bv;
+            }
           }
         }
         if (i >= 0 && gl == 0) {
-          if (rot) { nrm2[i] = al - t * ga; nrm2[j] = be + t * ga; *lastrot = sweep; }
+          if (rot) {
+            nrm2[i] = al - t * ga; nrm2[j] = be + t * ga; *lastrot = sweep;
+            if (SCALED) {
+              const T ndi = di * cs, ndj = dj * cs;
+              T nei = ei * sn, nej = ej * sn;
+              nei *= fma(-ndi, nei, T(2));
+              nej *= fma(-ndj, nej, T(2));
+              scl[2 * i] = ndi; scl[2 * i + 1] = nei;
+              scl[2 * j] = ndj; scl[2 * j + 1] = nej;
+            }
+          }
           else if (full) { nrm2[i] = al <= floor2 ? kNoise : al; nrm2[j] = be <= floor2 ? kNoise : be; }
         }
       }
+      sync();
+    }
+    if (SCALED && *lastrot == sweep) {
+      // fold the scales into the rows (all threads agree on lastrot)
+      for (int i = ht >> 5; i < nr; i += NT / 32) {
+        const T d = scl[2 * i];
+        if (d != T(1))
+          for (int x = ht & 31; x < nc + nu; x += 32) B[int64_t(i) * ldb + x] *= d;
+      }
+      sync();
+      for (int i = ht; i < nr; i += NT) { scl[2 * i] = T(1); scl[2 * i + 1] = T(1); }
       sync();
     }
     if (*lastrot < sweep) return sweep + 1;  // no rotation in this sweep (all threads agree)
@@ -432,6 +487,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   __shared__ int sh_src[2 * CH];    // Jacobi row order, then kept bond index -> candidate row
   __shared__ long long sh_key[2 * CH];   // ordering keys of the singular values
   __shared__ TC Bnrm[2 * CH];        // squared row norms cached by the Jacobi sweeps
+  __shared__ TC sh_scl[4 * CH];      // Jacobi row scales (d, 1/d) of float64 rows, per sector
   __shared__ TC sh_tv, sh_th, sh_smax;
   __shared__ long long sh_clk[5];    // cycles per phase of the current row (diagnostics)
   // cluster mode: task (rank 1 reads) and result (rank 0 reads) mailboxes
@@ -482,7 +538,8 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         const int rows = sh_task[0], N = sh_task[1], row0 = sh_task[3];
         if (tid == 0) sh_lastrot[0] = -1;
         const int nsw = tid < 256
-                            ? jacobi_rows<TC, 8>(Th, rows, N, rows, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src)
+                            ? jacobi_rows<TC, 8>(Th, rows, N, rows, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src,
+                                                 sh_scl)
                             : 0;
         __syncthreads();
         // the rotated rows back into the owner's Theta, sector 1 at its row row0
@@ -784,7 +841,8 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           // 8 lanes per row pair on one half (measured: faster than 4 lanes, and than
           // 16 lanes over the whole CTA, whose barrier costs more than its warps gain)
           const int nsw0 = half == 0
-                               ? jacobi_rows<TC, 8>(Th, k0, N, k0, LDT, 0, ht, &sh_lastrot[0], Bnrm, sh_src)
+                               ? jacobi_rows<TC, 8>(Th, k0, N, k0, LDT, 0, ht, &sh_lastrot[0], Bnrm, sh_src,
+                                                    sh_scl)
                                : 0;
           if (tid == 0) {
             if (nsw0 > 0) { sh_sweeps += nsw0; sh_svds += 1; }
@@ -800,14 +858,16 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           __syncthreads();
           if (send && sh_helper_dead) {   // the helper gave up: rotate sector 1 here
             const int nsw1 = jacobi_rows<TC, 16, 512>(Th + int64_t(k0) * LDT, k1, N, k1, LDT, 0, tid,
-                                                      &sh_lastrot[1], Bnrm + CH, sh_src + k0);
+                                                      &sh_lastrot[1], Bnrm + CH, sh_src + k0,
+                                                      sh_scl + 2 * CH);
             if (tid == 0 && nsw1 > 0) { sh_sweeps += nsw1; sh_svds += 1; }
           }
         } else {
           const int rows = half ? k1 : k0;
           TC *Bq = Th + int64_t(half ? k0 : 0) * LDT;
           const int nsw = jacobi_rows<TC, 4>(Bq, rows, N, rows, LDT, half, ht, &sh_lastrot[half],
-                                             Bnrm + (half ? CH : 0), sh_src + (half ? k0 : 0));
+                                             Bnrm + (half ? CH : 0), sh_src + (half ? k0 : 0),
+                                             sh_scl + (half ? 2 * CH : 0));
           if (ht == 0 && nsw > 0) { atomicAdd(&sh_sweeps, nsw); atomicAdd(&sh_svds, 1); }
         }
         __syncthreads();
