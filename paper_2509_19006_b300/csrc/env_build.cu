@@ -204,9 +204,13 @@ __device__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int 
 // Jacobi rotation (c, s, t = s / c) that orthogonalises two rows with squared
 // norms alpha, beta and inner product gamma. The angle only needs about float32
 // accuracy (an inexact angle leaves a small residual for the next sweep); what
-// must hold to working precision is c^2 (1 + t^2) = 1, or the rotation would not
-// be orthogonal. This keeps the float64 square roots and divisions (each a long
-// sequence on the float64 pipe) off the critical path of every Jacobi round.
+// must hold to working precision is c^2 + s^2 = 1, or the rotation would not
+// be orthogonal. For float64, zeta and t come from float32 arithmetic after an
+// exact power-of-two rescale, and the pair (c0, s0) is rescaled by the series
+// 1 / sqrt(n) = 1 - d/2 + 3 d^2 / 8 (d = n - 1, small), which leaves
+// c^2 + s^2 - 1 at rounding level. This keeps the float64 square roots and
+// divisions (each a long sequence on the float64 pipe) off the critical path of
+// every Jacobi round.
 template <typename T>
 __device__ __forceinline__ void rotation_params(T al, T be, T ga, T &cs, T &sn, T &t);
 template <>
@@ -225,6 +229,40 @@ __device__ __forceinline__ void rotation_params<float>(float al, float be, float
   if (num == 0.f) tf = 1.f;
   cs = rsqrtf(fmaf(tf, tf, 1.f));
   sn = cs * tf;
+  t = tf;
+}
+
+template <>
+__device__ __forceinline__ void rotation_params<double>(double al, double be, double ga, double &cs,
+                                                        double &sn, double &t) {
+  // zeta = num / den in float32: both are brought into float range by the
+  // exponent of the larger one, read from its bit pattern (a power-of-two
+  // scaling is exact); float64 arithmetic is left only for that scaling and
+  // the orthogonality rescale below
+  const double num = be - al, den = 2.0 * ga;
+  const double big = fmax(fabs(num), fabs(den));
+  int e = ((__double2hiint(big) >> 20) & 0x7ff) - 1023;
+  e = max(min(e, 1022), -1022);
+  const double sc = __hiloint2double((1023 - e) << 20, 0);   // 2^-e
+  const float fn = (float)(num * sc), fd = (float)(den * sc);
+  const float zeta = __fdividef(fn, fd);
+  const float az = fabsf(zeta);
+  float tf;
+  if (az > 1e15f) {
+    tf = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.f);
+    tf = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
+  }
+  if (fn == 0.f) tf = 1.f;
+  const float c0f = rsqrtf(fmaf(tf, tf, 1.f));
+  const double c0 = c0f, s0 = (double)(c0f * tf);
+  // c^2 + s^2 = 1 to working precision: rescale by 1/sqrt(1+d) ~ 1 - d/2 + 3d^2/8
+  // (|d| ~ 1e-7 from the float32 pair; the series' remainder 5|d|^3/16 < 1e-20)
+  const double d = fma(c0, c0, fma(s0, s0, -1.0));
+  const double r = fma(d, fma(0.375, d, -0.5), 1.0);
+  cs = c0 * r;
+  sn = s0 * r;
   t = tf;
 }
 
@@ -275,12 +313,14 @@ __device__ __forceinline__ void rotation_tangent_f64(double al, double be, doubl
 // beta <- beta + t gamma (Golub & Van Loan, Sec. 8.6.3; de Rijk's cached
 // norms, refreshed in the first round of every sweep).
 //
-// Float64 rows use scaled ("fast") rotations: row i is held as d_i x B_i, and
+// With SCALED (float64 rows) the rotations are scaled ("fast"): row i is held as d_i x B_i, and
 // a rotation becomes two multiply-adds per element pair,
 //   B_a <- B_a - (t d_b / d_a) B_b,   B_b <- B_b + (t d_a / d_b) B_a,
 //   d_a <- c d_a,   d_b <- c d_b,
-// instead of four float64 operations (B300 issues about two float64
-// instructions per clock per SM, and applying rotations is most of a round).
+// instead of four float64 operations. This pays where both parity sectors share
+// one SM's float64 pipe (one CTA per realization: 7 % faster at L = 96, chi = 64);
+// with a sector per SM (CTA pairs) the rounds are latency-bound and the extra
+// per-pair scale arithmetic costs more than the shorter rotations save.
 // The transformation of the true rows d x B is exactly the rotation (c, s).
 // Each row also keeps e_i = 1 / d_i, updated by 1/c = c (1 + t^2) and then one
 // Newton step e <- e (2 - d e), so that d_i e_i = 1 to working precision. At the
@@ -292,12 +332,12 @@ __device__ __forceinline__ void rotation_tangent_f64(double al, double be, doubl
 // on B300 every idle warp's instruction costs the whole SM issue slots.
 // NT threads take part: 256 (one half of the CTA, ht = its thread index, synchronised by
 // the half's named barrier) or 512 (the whole CTA, ht = threadIdx.x, __syncthreads).
-// scl: 2 values per row (d_i, e_i), used by float64 rows only.
-template <typename T, int TPP, int NT = 256>
+// scl: 2 values per row (d_i, e_i), used with SCALED only.
+template <typename T, int TPP, int NT = 256, bool SCALED = false>
 __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int ht,
                            volatile int *lastrot, T *nrm2, const int *perm, T *scl) {
   static_assert(NT == 256 || NT == 512, "a half or the whole CTA");
-  constexpr bool SCALED = sizeof(T) == 8;
+  static_assert(!SCALED || sizeof(T) == 8, "scaled rotations are for float64 rows");
   if (nr <= 1) return 0;  // uniform over the half
   const int P = nr + (nr & 1);
   const int npairs = P / 2;
@@ -865,7 +905,8 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         } else {
           const int rows = half ? k1 : k0;
           TC *Bq = Th + int64_t(half ? k0 : 0) * LDT;
-          const int nsw = jacobi_rows<TC, 4>(Bq, rows, N, rows, LDT, half, ht, &sh_lastrot[half],
+          const int nsw = jacobi_rows<TC, 4, 256, sizeof(TC) == 8>(Bq, rows, N, rows, LDT, half, ht,
+                                                                  &sh_lastrot[half],
                                              Bnrm + (half ? CH : 0), sh_src + (half ? k0 : 0),
                                              sh_scl + (half ? 2 * CH : 0));
           if (ht == 0 && nsw > 0) { atomicAdd(&sh_sweeps, nsw); atomicAdd(&sh_svds, 1); }
@@ -919,10 +960,11 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
                 (double)si / (double)smax;
         }
         __syncthreads();
-        if (tid == 0) {
+        if (warp == 0) {
+          // kept counts per sector, the cut gap and the discarded weight, over warp 0
           int ne = 0, no = 0;
           double kept_min = 1e300, drop_max = 0.0, tot = 0.0, drop = 0.0;
-          for (int i = 0; i < m; ++i) {
+          for (int i = lane; i < m; i += 32) {
             const double s = (double)sn[i];
             tot += s * s;
             if (sh_keep[i] >= 0) {
@@ -933,21 +975,34 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
               drop_max = s > drop_max ? s : drop_max;
             }
           }
-          sh_newE = ne; sh_newO = no;
-          sh_dmax = max(sh_dmax, ne + no);
-          sh_dsum += ne + no;
-          if (drop_max > 0.0) {
-            const double gap = kept_min / drop_max - 1.0;
-            sh_gap = gap < sh_gap ? gap : sh_gap;
-            sh_ntr += 1;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            ne += __shfl_xor_sync(0xffffffffu, ne, o);
+            no += __shfl_xor_sync(0xffffffffu, no, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            drop += __shfl_xor_sync(0xffffffffu, drop, o);
+            const double km = __shfl_xor_sync(0xffffffffu, kept_min, o);
+            const double dm = __shfl_xor_sync(0xffffffffu, drop_max, o);
+            kept_min = km < kept_min ? km : kept_min;
+            drop_max = dm > drop_max ? dm : drop_max;
           }
-          if (tot > 0.0) { const double d = drop / tot; sh_disc = d > sh_disc ? d : sh_disc; }
-          if (smax > TC(0) && isfinite((double)smax)) sh_lam += log((double)smax);
-          else set_flag(lay.flags, n, FLAG_NUMERIC);
+          if (lane == 0) {
+            sh_newE = ne; sh_newO = no;
+            sh_dmax = max(sh_dmax, ne + no);
+            sh_dsum += ne + no;
+            if (drop_max > 0.0) {
+              const double gap = kept_min / drop_max - 1.0;
+              sh_gap = gap < sh_gap ? gap : sh_gap;
+              sh_ntr += 1;
+            }
+            if (tot > 0.0) { const double d = drop / tot; sh_disc = d > sh_disc ? d : sh_disc; }
+            if (smax > TC(0) && isfinite((double)smax)) sh_lam += log((double)smax);
+            else set_flag(lay.flags, n, FLAG_NUMERIC);
+          }
         }
         __syncthreads();
         const int ne = sh_newE, no = sh_newO, nk = ne + no;
-        if (tid == 0) {
+        if (tid == ENV_THREADS - 32) {   // the flop count, off warp 0
           for (int q = 0; q < 2; ++q) {
             const double rq = q ? k1 : k0;
             const double a = rq > N ? rq : N, b = rq > N ? N : rq;

@@ -171,9 +171,11 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
       const T tv = (r > 0) ? Num<T>::tanh_(beta * T(jd[(r - 1) * L + c + 1])) : T(0);
       T *cs = Cs + buf * CH * LDC;
       const T *src = crow + int64_t(c + 1) * chi * chi;
+      // only the D_l x D_r block is read: the cache is zero outside the bond dimensions
+      const int Dl1 = bl.x + bl.y, Dr1 = br.x + br.y;
       for (int e = tid; e < CH * CH; e += P::NT) {
         const int a = e / CH, b = e % CH;
-        T v = (a < chi && b < chi) ? src[a * chi + b] : T(0);
+        T v = (a < Dl1 && b < Dr1) ? src[a * chi + b] : T(0);
         if ((a >= bl.x) != (b >= br.x)) v *= tv;
         cs[b * LDC + a] = v;
       }
@@ -218,7 +220,9 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
           outv[t] = acc[j][t] * inv;
           flp[t] = (up0 && a >= bl.x) ? -outv[t] : outv[t];   // input flip of the next step
         }
-        if (act[j]) Vec4<T>::store(rs + (int64_t(c) * lay.max_samples + sid[j]) * CH + cg * TC, outv);
+        // columns past bond c+1's dimension are zero: not spilled (the left pass reads zeros)
+        if (act[j] && cg * TC < Dl1)
+          Vec4<T>::store(rs + (int64_t(c) * lay.max_samples + sid[j]) * CH + cg * TC, outv);
 #pragma unroll
         for (int t = 0; t < TC; ++t) vout[(cg * TC + t) * SB + sl] = flp[t];
       }
@@ -232,15 +236,16 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
       const int2 bl = bd[c], br = bd[c + 1];
       T *cs = Cs + buf * CH * LDC;
       const T *src = crow + int64_t(c) * chi * chi;
+      const int Dlc = bl.x + bl.y, Drc = br.x + br.y;
       for (int e = tid; e < CH * CH; e += P::NT) {
         const int a = e / CH, b = e % CH;
-        cs[a * LDC + b] = (a < chi && b < chi) ? src[a * chi + b] : T(0);
+        cs[a * LDC + b] = (a < Dlc && b < Drc) ? src[a * chi + b] : T(0);
       }
       // right environment tile of this thread
       T R[TS][TC];
 #pragma unroll
       for (int j = 0; j < TS; ++j) {
-        if (c < L - 1 && act[j]) {
+        if (c < L - 1 && act[j] && cg * TC < Drc) {
           Vec4<T>::load(rs + (int64_t(c) * lay.max_samples + sid[j]) * CH + cg * TC, R[j]);
         } else {
 #pragma unroll
