@@ -363,11 +363,11 @@ def run_ours(args, wl):
             peak, peak_src = FP64_NOMINAL_GFLOPS, "nominal float64 rate (recipe table, not measured)"
         proposals = wl.n_real * S * args.steps
         # DRAM bytes per launch of this kernel: the float32, chi = 64 instantiation was
-        # captured on 8 realizations at L = 128 (131072 site-rows, 2.198 GB read + written,
+        # captured on 8 realizations at L = 128 (131072 site-rows, 2.203 GB read + written,
         # profiles/env_build_fp32_L128.md); traffic grows with the site-rows written
         site_rows = sum(L * L for L in wl.Ls)
         if args.prec == "fp32" and t.plan_ch == 64 and not ckpt:
-            traffic = 2.198e9 / 131072 * site_rows
+            traffic = 2.203e9 / 131072 * site_rows
             traffic_src = "ncu capture at L=128 x 8 realizations, scaled by site-rows"
         else:
             traffic, traffic_src = None, "no capture of this instantiation"
