@@ -212,7 +212,8 @@ tnmc_status tnmc_mh_step(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
  *            largest bond dimension, mean bond dimension, Jacobi SVDs run,
  *            mean Jacobi sweeps per SVD, then SM cycles spent in: MPO
  *            application + R handling, QR + Q formation, Theta product +
- *            setup, Jacobi, selection + stores, and the row's algorithmic
+ *            setup (in float64 including the QR that preconditions the
+ *            Jacobi), Jacobi, selection + stores, and the row's algorithmic
  *            flops: textbook counts of its QRs (2mn^2 - 2n^3/3, twice for Q),
  *            SVDs (4a^2b + 8ab^2 + 9b^3, Golub-Reinsch) and products). */
 tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spectra,
