@@ -10,6 +10,7 @@ The names follow the C ABI in ``include/tnmc.h``.
 from __future__ import annotations
 
 import ctypes
+import functools
 import os
 from dataclasses import dataclass
 from typing import List, Optional, Sequence
@@ -140,6 +141,17 @@ def layout_info(Ls, chi, beta, prec, max_samples, ckpt_every=0):
     return a.value, b.value, c.value
 
 
+def _on_stream(fn):
+    """Run a method with the object's stream current: the buffers it allocates or fills
+    are then ordered with the library's launches on that stream, and the caching
+    allocator reuses them only after the work queued there (stream-ordered reuse)."""
+    @functools.wraps(fn)
+    def wrapped(self, *args, **kwargs):
+        with self.torch.cuda.stream(self.stream):
+            return fn(self, *args, **kwargs)
+    return wrapped
+
+
 def _ptr(t) -> int:
     return ctypes.c_void_p(t.data_ptr())
 
@@ -191,7 +203,8 @@ class TNMC:
         _check(self.lib.tnmc_workspace_size(ctypes.byref(self._cfg), ctypes.byref(nbytes)),
                "tnmc_workspace_size")
         self.ws_bytes = nbytes.value
-        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        with torch.cuda.stream(self.stream):
+            self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
         base = self.ws.data_ptr()
         self._ws_ptr = (base + 255) // 256 * 256
         h = ctypes.c_void_p(0)
@@ -213,6 +226,7 @@ class TNMC:
             pass
 
     # ------------------------------------------------------------------ calls
+    @_on_stream
     def build_envs(self, J):
         """J: float32 device tensor (sum L^2, 4) in the paper's (left, up, right, down) layout."""
         assert J.dtype == self.torch.float32 and J.is_cuda and J.is_contiguous()
@@ -220,17 +234,20 @@ class TNMC:
         self._J_keep = J
         _check(self.lib.tnmc_build_envs(self.h, _ptr(J)), "tnmc_build_envs")
 
+    @_on_stream
     def log_z(self, out=None):
         out = out if out is not None else self.torch.empty(self.n_real, dtype=self.torch.float64, device=self.device)
         _check(self.lib.tnmc_log_z(self.h, _ptr(out)), "tnmc_log_z")
         return out
 
+    @_on_stream
     def alloc_proposals(self, S: int, prop_base: int = 0) -> Proposals:
         t = self.torch
         return Proposals(t.empty(S * self.sum_L2, dtype=t.uint8, device=self.device),
                          t.empty((self.n_real, S), dtype=t.float64, device=self.device),
                          t.empty((self.n_real, S), dtype=t.float64, device=self.device), S, prop_base)
 
+    @_on_stream
     def propose(self, S: int, seed: int, prop_base: int = 0, out: Optional[Proposals] = None) -> Proposals:
         out = out if out is not None else self.alloc_proposals(S, prop_base)
         out.S, out.prop_base = S, prop_base
@@ -238,6 +255,7 @@ class TNMC:
                                      _ptr(out.logq), _ptr(out.E)), "tnmc_propose")
         return out
 
+    @_on_stream
     def propose_static(self, S: int, seed: int, prop_base: int = 0, out: Optional[Proposals] = None) -> Proposals:
         """tnmc_propose with the library's fixed scratch array (no workspace scratch needed)."""
         out = out if out is not None else self.alloc_proposals(S, prop_base)
@@ -246,6 +264,7 @@ class TNMC:
                                             _ptr(out.logq), _ptr(out.E)), "tnmc_propose_static")
         return out
 
+    @_on_stream
     def score(self, spins, S: int):
         t = self.torch
         lq = t.empty((self.n_real, S), dtype=t.float64, device=self.device)
@@ -253,6 +272,7 @@ class TNMC:
         _check(self.lib.tnmc_score(self.h, int(S), _ptr(spins), _ptr(lq), _ptr(E)), "tnmc_score")
         return lq, E
 
+    @_on_stream
     def mh_init(self, seed: int) -> ChainState:
         t = self.torch
         st = ChainState(t.empty(self.sum_L2, dtype=t.uint8, device=self.device),
@@ -263,6 +283,7 @@ class TNMC:
                "tnmc_mh_init")
         return st
 
+    @_on_stream
     def mh_init_empty(self) -> ChainState:
         """A chain without a configuration: the first proposal of the next mh_step is accepted."""
         t = self.torch
@@ -274,6 +295,7 @@ class TNMC:
                "tnmc_mh_init_empty")
         return st
 
+    @_on_stream
     def mh_step(self, props: Proposals, state: ChainState, seed: int, accept=None):
         t = self.torch
         acc = accept if accept is not None else t.empty((self.n_real, props.S), dtype=t.uint8, device=self.device)
@@ -283,6 +305,7 @@ class TNMC:
                                      _ptr(state.n_accept)), "tnmc_mh_step")
         return acc
 
+    @_on_stream
     def set_diagnostics(self, S: int = 0, logits: bool = False, spectra: bool = False, rowinfo: bool = False):
         """Allocate and register the optional diagnostic outputs (None disables)."""
         t = self.torch
@@ -296,6 +319,7 @@ class TNMC:
                                              _ptr(ri) if ri is not None else z), "tnmc_set_diagnostics")
         return self._diag
 
+    @_on_stream
     def set_correction(self, params_bf16=None):
         """Use the learned correction (a bfloat16 parameter tensor, see MLP) or stop (None)."""
         if params_bf16 is None:
@@ -306,6 +330,7 @@ class TNMC:
         self._corr_keep = params_bf16
         _check(self.lib.tnmc_set_correction(self.h, _ptr(params_bf16), 1), "tnmc_set_correction")
 
+    @_on_stream
     def score_logits(self, spins, S: int):
         """Teacher-forced (log q, E, logits) of S configurations per realization."""
         t = self.torch
@@ -322,6 +347,7 @@ class TNMC:
                 self.lib.tnmc_set_diagnostics(self.h, *[_ptr(x) if x is not None else z for x in saved])
         return lq, E, lg
 
+    @_on_stream
     def mlp_features(self, spins, logits, S: int):
         """Training features (sum_n S L_n^2, 8) of S configurations per realization."""
         t = self.torch
@@ -330,6 +356,7 @@ class TNMC:
                "tnmc_mlp_features")
         return feat
 
+    @_on_stream
     def observables(self, props: Proposals):
         """Per realization (n_real, 6): IS log Z, ESS, E/N, <q^2>, <q^4>, Binder ratio."""
         t = self.torch
@@ -379,29 +406,33 @@ class MLP:
         W1[:, :7] = rng.standard_normal((64, 7)) / np.sqrt(7.0)
         host[0:1024] = W1.reshape(-1)
         host[1088:5184] = (rng.standard_normal((64, 64)) / 8.0).reshape(-1)
-        self.params = torch.from_numpy(host).to(self.device)
-        self.m = torch.zeros_like(self.params)
-        self.v = torch.zeros_like(self.params)
-        self.grad_buf = torch.zeros_like(self.params)
-        self.loss_buf = torch.zeros(1, dtype=torch.float64, device=self.device)
-        self.scratch = torch.empty(int(self.lib.tnmc_mlp_scratch_floats()), dtype=torch.float32,
-                                   device=self.device)
-        self.bf16 = torch.empty(MLP_PARAMS, dtype=torch.bfloat16, device=self.device)
+        with torch.cuda.stream(self.stream):
+            self.params = torch.from_numpy(host).to(self.device)
+            self.m = torch.zeros_like(self.params)
+            self.v = torch.zeros_like(self.params)
+            self.grad_buf = torch.zeros_like(self.params)
+            self.loss_buf = torch.zeros(1, dtype=torch.float64, device=self.device)
+            self.scratch = torch.empty(int(self.lib.tnmc_mlp_scratch_floats()), dtype=torch.float32,
+                                       device=self.device)
+            self.bf16 = torch.empty(MLP_PARAMS, dtype=torch.bfloat16, device=self.device)
         self.step = 0
         self.pack()
 
     def _s(self):
         return ctypes.c_void_p(self.stream.cuda_stream)
 
+    @_on_stream
     def load(self, params_f32):
         """Set the master copy (float32 tensor or array of MLP_PARAMS values) and its bfloat16 copy."""
         t = self.torch
         self.params.copy_(t.as_tensor(params_f32, dtype=t.float32))
         self.pack()
 
+    @_on_stream
     def pack(self):
         _check(self.lib.tnmc_mlp_pack(_ptr(self.params), _ptr(self.bf16), self._s()), "tnmc_mlp_pack")
 
+    @_on_stream
     def grad(self, feat, target_logit, batch: int = 0, seed: int = 0, step: int = 0):
         """(gradient, loss) tensors of the mean BCE; batch 0 = every row in order."""
         n = feat.shape[0]
@@ -411,12 +442,14 @@ class MLP:
                "tnmc_mlp_grad")
         return self.grad_buf, self.loss_buf
 
+    @_on_stream
     def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
         self.step += 1
         _check(self.lib.tnmc_mlp_adam(_ptr(self.params), _ptr(self.m), _ptr(self.v),
                                       _ptr(self.grad_buf), self.step, lr, beta1, beta2, eps,
                                       _ptr(self.bf16), self._s()), "tnmc_mlp_adam")
 
+    @_on_stream
     def train(self, feat, target_logit, steps: int, batch: int, lr: float, seed: int = 0,
               lr_final: float | None = None):
         """Adam on minibatches drawn on the device; returns the loss of every step (tensor)."""
@@ -429,6 +462,7 @@ class MLP:
             self.adam(rate)
         return losses
 
+    @_on_stream
     def forward(self, feat):
         """Delta of every feature row by the tensor-core network the sampler uses."""
         t = self.torch
