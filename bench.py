@@ -15,9 +15,13 @@ configurations of a chi = teacher-chi handle and both handles' conditionals)
 and times steps whose proposals carry the correction; the line reports the
 training time and the plain / corrected / teacher acceptance.
 
-Under torchrun (N > 1) each rank runs its own batch of the same size with its
-own disorder seeds (weak scaling, no collective on the data path); rank 0
-prints the line with the whole-job throughput (the slowest rank's time).
+Under torchrun (N > 1) the realization set grows with N (weak scaling): N times
+the workload's realizations, realization g drawn from seed 1000 + g, split over
+the ranks by longest-processing-time-first on the build cost
+(paper_2509_19006_b300.shard); each rank's handle names its realizations by g,
+so their random numbers do not depend on N. No collective touches the data
+path; the per-realization log Z and accepted counts are gathered at the end and
+rank 0 prints the line with the whole-job throughput (the slowest rank's time).
 """
 from __future__ import annotations
 
@@ -40,8 +44,38 @@ from workloads import SAMPLING_SEED, config  # noqa: E402
 def metric_name(wl) -> str:
     return (f"accepted samples/s at L={wl.Ls[0]},chi={wl.chi} "
             "(end to end: environments + proposals + MH)")
-FP64_NOMINAL_GFLOPS = 1250.0          # B300 float64 (recipe table)
-FP32_PEAK_GFLOPS = 148 * 128 * 2 * 2.032  # 148 SMs x 128 FP32 lanes x FMA x 2.032 GHz
+# Acceptance of the float64 method at the L = 256 workload, measured on the GPU (the
+# oracle computes the same method; its own MH at that size would take hours). Both
+# oracle legs (cpu_baseline and --impl reference) credit this one value.
+REF_ACCEPTANCE_L256 = 0.205
+
+
+def measure_alu_peaks(dev):
+    """Dense GEMM rates of this GPU in float64 and float32 (cuBLAS through torch, TF32
+    off): the measured ALU ceilings the environment build is compared with, in GFLOP/s."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt, n, reps in (("fp64", torch.float64, 4096, 3), ("fp32", torch.float32, 8192, 5)):
+            a = torch.randn(n, n, dtype=dt, device=dev)
+            b = torch.randn(n, n, dtype=dt, device=dev)
+            torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[name] = 2.0 * n ** 3 / best / 1e9
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
 
 
 def load_peaks():
@@ -186,7 +220,7 @@ def train_correction(P, t, J, wl, args, dev):
     import torch
     S = wl.S
     t0 = time.perf_counter()
-    teacher = P.TNMC(wl.Ls, args.teacher_chi, wl.beta, args.prec, max_samples=S, device=dev,
+    teacher = P.TNMC(t.Ls, args.teacher_chi, wl.beta, args.prec, max_samples=S, device=dev,
                      cutoff=args.cutoff)
     t.build_envs(J)
     teacher.build_envs(J)
@@ -212,7 +246,7 @@ def train_correction(P, t, J, wl, args, dev):
         pr = h.propose(S, 11, 5_000_000 + S)
         h.mh_step(pr, st, 11)
         torch.cuda.synchronize()
-        return (st.n_accept.sum().item() - n0) / (S * wl.n_real)
+        return (st.n_accept.sum().item() - n0) / (S * h.n_real)
 
     a_plain = acceptance(t, None)
     a_teacher = acceptance(teacher, None)
@@ -222,7 +256,7 @@ def train_correction(P, t, J, wl, args, dev):
     t.set_correction(net.bf16)
     t._net_keep = net
     return {"teacher_chi": args.teacher_chi, "train_steps": args.train_steps, "batch": 65536,
-            "examples": S * sum(L * L for L in wl.Ls),
+            "examples": S * sum(L * L for L in t.Ls),
             "data_s": t_data, "train_s": t_train,
             "acceptance_plain": a_plain, "acceptance_corrected": a_corr,
             "acceptance_teacher": a_teacher}
@@ -238,23 +272,33 @@ def run_ours(args, wl):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    # weak scaling: every rank a full batch with its own disorder seeds
-    wl.base_seed = wl.base_seed + rank * 100000
-    Jhost = torch.from_numpy(wl.packed_J()).pin_memory()
+    # weak scaling over one realization set: world x the workload's realizations,
+    # split by LPT; realization g keeps its seed and random-number stream at any world size
+    from paper_2509_19006_b300 import shard
+    from workloads import Workload
+    n_all = world * wl.n_real
+    gw = Workload(wl.name, [wl.Ls[g % wl.n_real] for g in range(n_all)], wl.beta, wl.chi, wl.S,
+                  kind=wl.kind, base_seed=wl.base_seed, p=wl.p)
+    ids = shard.lpt_partition(gw.Ls, gw.chi, world)[rank]
+    my_Ls = [gw.Ls[g] for g in ids]
+    peaks_alu = measure_alu_peaks(dev)
+    Jhost = torch.from_numpy(gw.packed_J(ids)).pin_memory()
     J = Jhost.to(dev)
     S = wl.S
     ckpt = args.ckpt if args.ckpt >= 0 else (32 if max(wl.Ls) >= 1024 else 0)
-    t = P.TNMC(wl.Ls, wl.chi, wl.beta, args.prec, max_samples=S, device=dev, cutoff=args.cutoff,
+    t = P.TNMC(my_Ls, wl.chi, wl.beta, args.prec, max_samples=S, device=dev, cutoff=args.cutoff,
                ckpt_every=ckpt)
+    t.set_realization_ids(ids)
+    n_mine = len(ids)
     stream = t.stream
     learned = None
     if args.learned:
         learned = train_correction(P, t, J, wl, args, dev)
     props = t.alloc_proposals(S)
     state = None
-    acc = torch.empty((wl.n_real, S), dtype=torch.uint8, device=dev)
+    acc = torch.empty((n_mine, S), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
-    logz = torch.empty(wl.n_real, dtype=torch.float64, device=dev)
+    logz = torch.empty(n_mine, dtype=torch.float64, device=dev)
 
     def step(base):
         nonlocal state
@@ -284,7 +328,7 @@ def run_ours(args, wl):
 
     # ---------------- device-resident timed region
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    env_ms, step_ms, prop_ms, accepted = [], [], [], 0
+    env_ms, step_ms, prop_ms, samp_ms, accepted = [], [], [], [], 0
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
@@ -296,11 +340,12 @@ def run_ours(args, wl):
         t_all0.record(stream)
         for k in range(args.steps):
             flush.zero_()
-            e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+            e0, e1, e2, e3, e4 = ev(), ev(), ev(), ev(), ev()
             e0.record(stream)
             t.build_envs(J)
             e1.record(stream)
             t.log_z(out=logz)
+            e4.record(stream)
             t.propose(S, SAMPLING_SEED, 10_000_000 * (k + 1), out=props)
             e3.record(stream)
             t.mh_step(props, state, SAMPLING_SEED, accept=acc)
@@ -308,6 +353,7 @@ def run_ours(args, wl):
             env_ms.append((e0, e1))
             step_ms.append((e0, e2))
             prop_ms.append((e1, e3))
+            samp_ms.append((e4, e3))
         t_all1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -316,19 +362,22 @@ def run_ours(args, wl):
     accepted = int((state.n_accept - n_acc0).sum().item())
     env_t = [a.elapsed_time(b) for a, b in env_ms]
     prop_t = [a.elapsed_time(b) for a, b in prop_ms]
+    samp_t = [a.elapsed_time(b) for a, b in samp_ms]
     step_t = [a.elapsed_time(b) for a, b in step_ms]
     total_ms = t_all0.elapsed_time(t_all1)   # includes the L2 flushes between steps
     my_ms = sum(step_t)
 
     # ---------------- end to end through the public API with host buffers
-    h_acc = torch.empty((wl.n_real, S), dtype=torch.uint8).pin_memory()
-    h_nacc = torch.empty(wl.n_real, dtype=torch.int64).pin_memory()
-    h_logz = torch.empty(wl.n_real, dtype=torch.float64).pin_memory()
+    # (a bounded number of steps: the same metric, its wall time and proposal count stated)
+    e2e_steps = min(args.steps, args.e2e_steps)
+    h_acc = torch.empty((n_mine, S), dtype=torch.uint8).pin_memory()
+    h_nacc = torch.empty(n_mine, dtype=torch.int64).pin_memory()
+    h_logz = torch.empty(n_mine, dtype=torch.float64).pin_memory()
     e2e_acc = 0
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        for k in range(args.steps):
+        for k in range(e2e_steps):
             n0 = state.n_accept.clone()
             J.copy_(Jhost, non_blocking=True)
             t.build_envs(J)
@@ -344,42 +393,53 @@ def run_ours(args, wl):
     h2d = Jhost.numel() * 4
     d2h = h_acc.numel() + h_nacc.numel() * 8 + h_logz.numel() * 8
 
-    # ---------------- gather over ranks (max time, summed work)
+    # ---------------- gather over ranks (max time, summed work, per-realization results)
     vec = torch.tensor([my_ms, float(accepted), e2e_s, float(e2e_acc)], dtype=torch.float64, device=dev)
+    per_real = torch.stack([logz.double(), (state.n_accept - n_acc0).double()], dim=1)
+    full = shard.gather(dist if world > 1 else None, n_all, ids, per_real, device=dev)
     if world > 1:
         mx = vec.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
         sm = vec.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
         my_ms_all, accepted_all, e2e_s_all, e2e_acc_all = mx[0].item(), sm[1].item(), mx[2].item(), sm[3].item()
     else:
         my_ms_all, accepted_all, e2e_s_all, e2e_acc_all = my_ms, accepted, e2e_s, e2e_acc
+    assert int(full[:, 1].sum().item()) == int(accepted_all)
 
     if rank == 0:
         peaks = load_peaks()
         env_avg_s = sum(env_t) / len(env_t) / 1e3
+        samp_avg_s = sum(samp_t) / len(samp_t) / 1e3
         achieved = flops_env / env_avg_s / 1e9
         if args.prec == "fp32":
-            peak, peak_src = FP32_PEAK_GFLOPS, "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"
+            peak, peak_src = peaks_alu["fp32"], "measured: cuBLAS float32 GEMM (TF32 off) on this GPU"
         else:
-            peak, peak_src = FP64_NOMINAL_GFLOPS, "nominal float64 rate (recipe table, not measured)"
-        proposals = wl.n_real * S * args.steps
-        # DRAM bytes per launch of this kernel: the float32, chi = 64 instantiation was
-        # captured on 8 realizations at L = 128 (131072 site-rows, 2.203 GB read + written,
-        # profiles/env_build_fp32_L128.md); traffic grows with the site-rows written
-        site_rows = sum(L * L for L in wl.Ls)
+            peak, peak_src = peaks_alu["fp64"], "measured: cuBLAS float64 GEMM on this GPU"
+        proposals = n_mine * S * args.steps
+        # DRAM bytes per launch of the float32, chi = 64 build: an ncu capture of 8
+        # realizations at L = 128 (131072 site-rows) read + wrote 2.203 GB; traffic grows
+        # with the site-rows written
+        site_rows = sum(L * L for L in my_Ls)
         if args.prec == "fp32" and t.plan_ch == 64 and not ckpt:
             traffic = 2.203e9 / 131072 * site_rows
             traffic_src = "ncu capture at L=128 x 8 realizations, scaled by site-rows"
         else:
             traffic, traffic_src = None, "no capture of this instantiation"
+        # sampler: algorithmic bytes per sample-site = the right environment spilled and read
+        # back (2 D values: L D values per chain do not fit on chip), the cache read once per
+        # pass per realization (2 D^2 values, shared by the S chains) and the spin written
+        esz = 8 if args.prec == "fp64" else 4
+        samp_sites = S * site_rows
+        samp_bytes = samp_sites * (2.0 * dmean * esz + 2.0 * dmean * dmean * esz / S + 1.0)
+        hbm_peak = peaks.get("hbm_gbs") or 6484.6
         cpu = None
         if world == 1 and args.cpu_baseline:
             t_real, rows_done, _ = oracle_sample(wl, seconds=args.ref_seconds)
-            acc_rate = accepted / proposals
-            cpu = {"value": S * acc_rate / t_real, "unit": "accepted/s", "cores": cpu_cores(),
+            cpu = {"value": S * args.ref_acceptance / t_real, "unit": "accepted/s", "cores": cpu_cores(),
                    "kind": "oracle",
                    "sample": (f"FP64 oracle, realization 0 of {wl.name}: bottom {rows_done} environment "
                               f"rows timed and extrapolated to {wl.Ls[0]} rows (proposals not timed); "
-                              f"acceptance taken from this run ({acc_rate:.4f})")}
+                              f"credited with the float64 method's acceptance {args.ref_acceptance} "
+                              f"(the value the reference arm credits)")}
         line = {
             "metric": metric_name(wl),
             "value": accepted_all / (my_ms_all / 1e3),
@@ -391,7 +451,7 @@ def run_ours(args, wl):
             "data": ("synthetic Gaussian N(0,1) disorder, seeded" if wl.kind == "gauss"
                      else "synthetic +-J disorder (p = 1/2), seeded"),
             "config": {"workload": wl.name, "L": wl.Ls[0], "chi": wl.chi, "beta": wl.beta,
-                       "realizations_per_gpu": wl.n_real, "samples_per_realization": S,
+                       "realizations_per_gpu": wl.n_real, "realizations": n_all, "samples_per_realization": S,
                        "precision": args.prec, "cutoff": t.cutoff, "ckpt_every": ckpt,
                        "learned_correction": bool(args.learned),
                        "l2": "flushed (256 MB write) before every timed step; environment cache >> L2"},
@@ -410,7 +470,18 @@ def run_ours(args, wl):
                          "algorithmic_flops_per_launch": flops_env},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_acc_all / e2e_s_all, "unit": "accepted/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps, "wall_s": e2e_s_all, "accepted": int(e2e_acc_all),
+                    "proposals": n_all * S * e2e_steps},
+            "roofline_sampling": {"kernel": "sample_kernel (proposals)", "bound": "hbm",
+                                  "achieved": samp_bytes / samp_avg_s / 1e9, "peak": hbm_peak,
+                                  "unit": "GB/s", "frac": samp_bytes / samp_avg_s / 1e9 / hbm_peak,
+                                  "algorithmic_bytes_per_launch": samp_bytes,
+                                  "launch_ms": samp_avg_s * 1e3},
+            "alu_peaks_measured_gflops": peaks_alu,
+            "per_realization": {"log_z_mean": float(full[:, 0].mean().item()),
+                                "accepted_min": int(full[:, 1].min().item()),
+                                "accepted_max": int(full[:, 1].max().item())},
             "gpu_launches": args.steps * (2 + 1 + 1 + 1 + (2 * ((max(wl.Ls) + ckpt - 1) // ckpt) - 1
                                                           if ckpt else 0)),
             "clocks": clk,
@@ -621,9 +692,9 @@ def main():
     ap.add_argument("--cutoff", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
-    # acceptance of the float64 method at the L=256 workload (the oracle computes the same
-    # method; its own MH at this size would take hours): 0.205 on the GPU
-    ap.add_argument("--ref-acceptance", type=float, default=0.205)
+    ap.add_argument("--ref-acceptance", type=float, default=REF_ACCEPTANCE_L256)
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="steps of the end-to-end leg (host buffers), at most --steps")
     ap.add_argument("--ckpt", type=int, default=-1,
                     help="cache every K-th environment row (default: 32 for L >= 1024, else off)")
     ap.add_argument("--learned", action="store_true",

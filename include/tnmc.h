@@ -35,9 +35,10 @@
  *   holds S configurations per realization).
  * - Random numbers: Philox4x64-10 (Salmon et al., SC'11), key (seed, 0);
  *   spin draw of site i of proposal id t in realization n uses counter
- *   (i >> 2, t, n, 0) word i & 3; the accept test of proposal t uses
- *   (0, t, n, 1) word 0; the random initial state uses (i >> 2, 0, n, 2)
- *   word i & 3. A word w becomes u = (2 (w >> 12) + 1) 2^-53.
+ *   (i >> 2, t, g, 0) word i & 3; the accept test of proposal t uses
+ *   (0, t, g, 1) word 0; the random initial state uses (i >> 2, 0, g, 2)
+ *   word i & 3, where g is the realization's stream id (its index n unless
+ *   set by tnmc_set_realization_ids). A word w becomes u = (2 (w >> 12) + 1) 2^-53.
  */
 #ifndef TNMC_H
 #define TNMC_H
@@ -318,7 +319,9 @@ tnmc_status tnmc_mlp_forward(const float *d_feat, int64_t n_ex, const void *d_pa
  * on the GPU -- two streams, or two handles at the same time -- race on the
  * array and must be ordered by the caller. The first call on a device looks
  * up the array's device address once (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.
+ * current) and keeps it for the life of the process; make that first call before
+ * any stream capture. A device reset (or a release of the primary context) after
+ * that first call is not supported: later calls would use the old address.
  * Errors: TNMC_ERR_ARG, TNMC_ERR_STATE, TNMC_ERR_CUDA. */
 tnmc_status tnmc_propose_static(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop_base,
                                 uint8_t *d_spins, double *d_logq, double *d_E);
@@ -336,6 +339,16 @@ size_t tnmc_propose_static_limit(void);
  * set a tiny budget to make the waits run out (the paper has no counterpart).
  * Errors: TNMC_ERR_ARG. */
 tnmc_status tnmc_set_wait_budget(tnmc_handle *h, int64_t cycles);
+
+/* Stream ids of the realizations (the paper has no counterpart; it runs one
+ * process): h_ids is a host array [n_real] of distinct non-negative ids, or NULL
+ * for 0 .. n_real-1 (the default). A realization's random numbers depend on its
+ * stream id, not on its position in this handle, so a batch split over several
+ * processes (each handle holding a shard, ids = the realizations' indices in the
+ * whole set) draws exactly what one handle over the whole set draws. Takes effect
+ * for later calls; synchronises the handle's stream.
+ * Errors: TNMC_ERR_ARG (negative id), TNMC_ERR_CUDA. */
+tnmc_status tnmc_set_realization_ids(tnmc_handle *h, const int64_t *h_ids);
 
 /* Copy the per-realization device flags (TNMC_FLAG_*) to h_flags [n_real],
  * after synchronising the stream; clears them when clear != 0.

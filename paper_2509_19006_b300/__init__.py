@@ -30,7 +30,7 @@ EXPORTED = [
     "tnmc_propose_static", "tnmc_propose_static_limit", "tnmc_set_correction",
     "tnmc_mlp_features", "tnmc_mlp_scratch_floats", "tnmc_mlp_grad", "tnmc_mlp_adam",
     "tnmc_mlp_pack", "tnmc_mlp_forward", "tnmc_mh_init_empty", "tnmc_set_wait_budget",
-    "tnmc_observables",
+    "tnmc_observables", "tnmc_set_realization_ids",
 ]
 
 # learned proposal correction: parameter vector layout (include/tnmc.h)
@@ -84,6 +84,7 @@ def load_library():
         "tnmc_mh_init": ([vp, u64, vp, vp, vp], i32),
         "tnmc_mh_init_empty": ([vp, vp, vp, vp], i32),
         "tnmc_set_wait_budget": ([vp, ctypes.c_int64], i32),
+        "tnmc_set_realization_ids": ([vp, vp], i32),
         "tnmc_observables": ([vp, i32, vp, vp, vp, vp], i32),
         "tnmc_mh_step": ([vp, i32, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "tnmc_set_diagnostics": ([vp, vp, vp, vp], i32),
@@ -144,11 +145,25 @@ def layout_info(Ls, chi, beta, prec, max_samples, ckpt_every=0):
 def _on_stream(fn):
     """Run a method with the object's stream current: the buffers it allocates or fills
     are then ordered with the library's launches on that stream, and the caching
-    allocator reuses them only after the work queued there (stream-ordered reuse)."""
+    allocator reuses them only after the work queued there (stream-ordered reuse).
+
+    When the caller's current stream is another one, the object's stream first waits
+    for the work queued on the caller's stream (inputs made there are complete before
+    the library reads them), and the caller's stream then waits for the library's work
+    (outputs are complete before the caller reads or frees them). Under stream capture
+    the caller orders its streams itself (cross-stream waits would join the capture)."""
     @functools.wraps(fn)
     def wrapped(self, *args, **kwargs):
-        with self.torch.cuda.stream(self.stream):
-            return fn(self, *args, **kwargs)
+        cuda = self.torch.cuda
+        cur = cuda.current_stream(self.device)
+        other = cur != self.stream and not cuda.is_current_stream_capturing()
+        if other:
+            self.stream.wait_stream(cur)
+        with cuda.stream(self.stream):
+            out = fn(self, *args, **kwargs)
+        if other:
+            cur.wait_stream(self.stream)
+        return out
     return wrapped
 
 
@@ -364,6 +379,18 @@ class TNMC:
         _check(self.lib.tnmc_observables(self.h, int(props.S), _ptr(props.spins), _ptr(props.logq),
                                          _ptr(props.E), _ptr(out)), "tnmc_observables")
         return out
+
+    def set_realization_ids(self, ids=None):
+        """Stream ids of the realizations (their indices in the whole set when this handle
+        holds a shard of it); None restores 0 .. n_real-1."""
+        import numpy as np
+        if ids is None:
+            _check(self.lib.tnmc_set_realization_ids(self.h, ctypes.c_void_p(0)), "tnmc_set_realization_ids")
+            return
+        arr = np.ascontiguousarray(np.asarray(ids, dtype=np.int64))
+        assert arr.shape == (self.n_real,)
+        _check(self.lib.tnmc_set_realization_ids(self.h, arr.ctypes.data_as(ctypes.c_void_p)),
+               "tnmc_set_realization_ids")
 
     def set_wait_budget(self, cycles: int):
         """Budget of the bounded device waits in SM cycles (0 = default, ~20 s)."""

@@ -122,6 +122,7 @@ cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 struct tnmc_handle {
   std::vector<int32_t> L;
+  std::vector<RealInfo> reals;   // host copy of the per-realization table
   tnmc_config cfg;
   Plan plan;
   Layout lay;
@@ -222,6 +223,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
     reals[n].line_off = ro;
     reals[n].cache_off = co;
     reals[n].ckpt_off = ko;
+    reals[n].gid = n;
     so += L * L; bo += L * (L + 1); ro += L;
     co += cache_rows(int(L), cfg->ckpt_every) * L;
     if (cfg->ckpt_every > 0 && cfg->prec == TNMC_MIXED) ko += int64_t((L + cfg->ckpt_every - 1) / cfg->ckpt_every) * L;
@@ -272,6 +274,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
     delete h;
     return TNMC_ERR_CUDA;
   }
+  h->reals = std::move(reals);
   *out = h;
   return TNMC_OK;
 }
@@ -307,6 +310,21 @@ tnmc_status tnmc_mlp_features(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
                  cudaSuccess
              ? TNMC_OK
              : TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_set_realization_ids(tnmc_handle *h, const int64_t *h_ids) {
+  if (!h) return TNMC_ERR_ARG;
+  for (int n = 0; n < h->cfg.n_real; ++n) {
+    const int64_t id = h_ids ? h_ids[n] : n;
+    if (id < 0) return TNMC_ERR_ARG;
+    h->reals[n].gid = id;
+  }
+  // the table is read by later launches on this stream; the host copy lives in the handle
+  const cudaError_t e = cudaMemcpyAsync(const_cast<RealInfo *>(h->lay.reals), h->reals.data(),
+                                        h->reals.size() * sizeof(RealInfo), cudaMemcpyHostToDevice,
+                                        h->stream);
+  if (e == cudaSuccess) return cudaStreamSynchronize(h->stream) == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
+  return TNMC_ERR_CUDA;
 }
 
 tnmc_status tnmc_set_wait_budget(tnmc_handle *h, int64_t cycles) {

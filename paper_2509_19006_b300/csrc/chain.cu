@@ -86,13 +86,13 @@ __global__ void log_z_kernel(Layout lay, double *logz) {
 }
 
 // Random initial configuration: spin bit = top bit of the Philox word of
-// counter (i >> 2, 0, n, 2), word i & 3.
+// counter (i >> 2, 0, gid, 2), word i & 3 (gid: the realization's stream id).
 __global__ void init_state_kernel(Layout lay, uint64_t seed, uint8_t *spins) {
   const int n = blockIdx.x;
   const RealInfo ri = lay.reals[n];
   const int64_t L2 = int64_t(ri.L) * ri.L;
   for (int64_t g = threadIdx.x; g < (L2 + 3) / 4; g += blockDim.x) {
-    const U64x4 w = philox4x64_10((uint64_t)g, 0ull, (uint64_t)n, TAG_INIT, seed, 0ull);
+    const U64x4 w = philox4x64_10((uint64_t)g, 0ull, (uint64_t)ri.gid, TAG_INIT, seed, 0ull);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int64_t i = 4 * g + q;
@@ -119,7 +119,7 @@ __global__ void mh_kernel(Layout lay, int S, uint64_t seed, uint64_t base, const
       const double a = __dsub_rn(__dmul_rn(nb, Ep), lqp);
       const double b = __dsub_rn(__dmul_rn(nb, E), lq);
       const double lr = __dsub_rn(a, b);
-      const U64x4 w = philox4x64_10(0ull, base + (uint64_t)t, (uint64_t)n, TAG_MH, seed, 0ull);
+      const U64x4 w = philox4x64_10(0ull, base + (uint64_t)t, (uint64_t)ri.gid, TAG_MH, seed, 0ull);
       const double u = word_to_uniform(w.x[0]);
       const int acc = log(u) < lr ? 1 : 0;
       accept[int64_t(n) * S + t] = (uint8_t)acc;

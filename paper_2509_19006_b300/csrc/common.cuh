@@ -30,6 +30,8 @@ struct RealInfo {
   int64_t line_off;   // sum_{m<n} L_m: sampler scratch lines (per sample) before it
   int64_t cache_off;  // first chi x chi matrix of this realization in the cache
   int64_t ckpt_off;   // first chi x chi matrix of its float64 checkpoint rows (MIXED + checkpoints)
+  int64_t gid;        // stream id of its random numbers (the counter word that names the
+                      // realization): its index n unless the caller set global ids
 };
 
 // Device-side view of the workspace; passed by value to every kernel.

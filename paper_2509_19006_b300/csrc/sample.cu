@@ -375,7 +375,7 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
             const int64_t g = i >> 2;
             if (g != pg[o]) {
               const U64x4 ww = philox4x64_10((uint64_t)g, prop_base + (uint64_t)sid[j],
-                                             (uint64_t)n, TAG_SPIN, seed, 0ull);
+                                             (uint64_t)ri.gid, TAG_SPIN, seed, 0ull);
 #pragma unroll
               for (int q = 0; q < 4; ++q) pw[o][q] = ww.x[q];
               pg[o] = g;

@@ -1,0 +1,222 @@
+"""GPU parity at chi = 64: the kernel instantiations the benchmark runs, against the oracle.
+
+The L = 256 benchmark builds and samples with the chi = 64 instantiations
+(float32; float64 as 2-CTA clusters, or one CTA per realization beyond 74
+realizations; float64 build with a float32 cache). Here each of them meets the
+FP64 oracle on sizes the oracle finishes in seconds:
+
+* L = 12, 13: chi = 64 is exact (an L-site bond never needs more than
+  2^floor(L/2) = 64), so log Z is also pinned to the exact row transfer matrix;
+* L = 48, beta = 1: the bonds reach 64 and chi truncates;
+* L = 64, beta = 3: the cutoff truncates (bonds up to 56), the regime of the
+  benchmark.
+Bounds as in the smaller-chi parity tests: float64 log Z to 1e-10 relative,
+spectra to 1e-8 where the cut gap exceeds 1e-6 (2e-7 absolute at beta = 3),
+free-running proposals bit-exact up to draws within 1e-9 of their probability;
+float32 |d log Z| / L^2 <= 1e-6 and the teacher-forced draw audit.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bmps, exact, philox, sampler  # noqa: E402
+import parity  # noqa: E402
+
+CHI = 64
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2509_19006_b300 import build
+    build.build()
+    import paper_2509_19006_b300 as P
+    return P
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle(Ls, beta, kind, cutoff):
+    reals = parity.realizations(list(Ls), kind)
+    return reals, parity.oracle_envs(reals, beta, CHI, cutoff)
+
+
+def _gpu(P, Ls, beta, prec, kind, S, diag=False, seed=42):
+    reals = parity.realizations(list(Ls), kind)
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(list(Ls), CHI, beta, prec, max_samples=S)
+    assert t.plan_ch == 64
+    d = t.set_diagnostics(S=S, spectra=True, rowinfo=True) if diag else None
+    t.build_envs(J)
+    lz = t.log_z().cpu().numpy()
+    props = t.propose(S, seed, 0)
+    torch.cuda.synchronize()
+    st, flags = t.device_status()
+    return t, lz, props, d, st, flags
+
+
+def _audit(t, Ls, reals, envs, beta, S, props, band=2e-3):
+    """float32 sampling: the teacher-forced draws take the oracle's decisions outside the band."""
+    o_props = [sampler.propose(rows, Jh, Jv, beta, S, 42, 0, n)
+               for n, ((Jh, Jv), rows) in enumerate(zip(reals, envs))]
+    spins_in = torch.from_numpy(np.concatenate([o[0].reshape(-1) for o in o_props])).cuda()
+    g_lq, g_E, g_lg = t.score_logits(spins_in, S)
+    g_E, g_lg = g_E.cpu().numpy(), g_lg.cpu().numpy()
+    g_sig = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
+    off = 0
+    for n, L in enumerate(Ls):
+        o_sig, _, o_E, o_lg = o_props[n]
+        np.testing.assert_array_equal(g_E[n], o_E)
+        u = philox.spin_uniforms(L, np.arange(S, dtype=np.uint64), n, 42)
+        lg = g_lg[off:off + S * L * L].reshape(S, L * L)
+        off += S * L * L
+        inband = np.abs(u - sampler.sigmoid(o_lg)) < band
+        assert np.array_equal((u < sampler.sigmoid(lg)).astype(np.uint8)[~inband],
+                              o_sig.reshape(S, -1)[~inband])
+        for k in range(S):
+            a, b = g_sig[n][k].reshape(-1), o_sig[k].reshape(-1)
+            if not np.array_equal(a, b):
+                assert inband[k, int(np.argmax(a != b))], (n, k)
+
+
+@pytest.mark.parametrize("prec,beta", [("fp64", 2.0), ("fp64", 3.0), ("mixed", 2.0), ("mixed", 3.0),
+                                       ("fp32", 2.0)])
+def test_chi64_exact_sizes(P, prec, beta):
+    """(float32 at beta = 3 is outside its stated bounds; its error is measured in
+    test_gpu_precision_table.py.)"""
+    Ls, S = (12, 13, 12), 64
+    t, lz, props, _, st, flags = _gpu(P, Ls, beta, prec, "pmj", S)
+    reals, envs = _oracle(Ls, beta, "pmj", t.cutoff)
+    assert st == 0 and not flags.any()
+    for n, (L, (Jh, Jv), rows) in enumerate(zip(Ls, reals, envs)):
+        o_lz = bmps.log_z(rows)
+        ex = exact.transfer_log_z(Jh, Jv, beta)
+        if prec == "fp32":
+            assert abs(lz[n] - o_lz) / (L * L) < 1e-6, (n, lz[n], o_lz)
+        else:   # float64 build; MIXED reads the top row from its float32 cache
+            rel = 1e-10 if prec == "fp64" else 1e-9
+            assert abs(lz[n] - o_lz) < rel * abs(o_lz), (n, lz[n], o_lz)
+        # the cutoff (1e-12 of the largest singular value) is the only approximation left
+        assert abs(lz[n] - ex) / (L * L) < 1e-6, (n, lz[n], ex)
+    if prec == "fp64":
+        spins = parity.split_spins(props.spins.cpu().numpy(), list(Ls), S)
+        lq, E = props.logq.cpu().numpy(), props.E.cpu().numpy()
+        nbd = 0
+        for n, ((Jh, Jv), rows) in enumerate(zip(reals, envs)):
+            _, b = parity.compare_proposals(rows, Jh, Jv, beta, 42, 0, n, spins[n], lq[n], E[n])
+            nbd += b
+        assert nbd <= 1
+    elif beta == 2.0:
+        _audit(t, list(Ls), reals, envs, beta, S, props)
+
+
+def test_chi64_fp64_one_cta_per_realization(P):
+    """More realizations than CTA pairs fit (80 > 74): the one-CTA float64 build at chi = 64."""
+    rng = np.random.default_rng(11)
+    Ls = tuple([12, 13] + [int(x) for x in rng.integers(2, 7, size=78)])
+    beta, S = 1.5, 24
+    t, lz, props, _, st, flags = _gpu(P, Ls, beta, "fp64", "gauss", S)
+    assert st == 0 and not flags.any()
+    reals, envs = _oracle(Ls, beta, "gauss", t.cutoff)
+    for n in range(len(Ls)):
+        assert abs(lz[n] - bmps.log_z(envs[n])) < 1e-10 * max(1.0, abs(lz[n])), n
+    sig = parity.split_spins(props.spins.cpu().numpy(), list(Ls), S)
+    lq, E = props.logq.cpu().numpy(), props.E.cpu().numpy()
+    for n in (0, 1, 40, 79):
+        Jh, Jv = reals[n]
+        n_eq, n_bd = parity.compare_proposals(envs[n], Jh, Jv, beta, 42, 0, n, sig[n], lq[n], E[n])
+        assert n_eq + n_bd == S and n_bd <= 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_chi64_truncating_L48_beta1(P, prec):
+    """L = 48, beta = 1: bonds reach chi = 64 and are cut there."""
+    Ls, beta, S = (48,), 1.0, 64
+    t, lz, props, (_, sp, ri), st, flags = _gpu(P, Ls, beta, prec, "pmj", S, diag=True)
+    assert st == 0 and not flags.any()
+    reals, envs = _oracle(Ls, beta, "pmj", t.cutoff)
+    (Jh, Jv), rows, L = reals[0], envs[0], Ls[0]
+    ri = ri.cpu().numpy().reshape(-1, 14)
+    assert ri[:, 4].max() == CHI                   # the bond dimension reached chi
+    o_lz = bmps.log_z(rows)
+    if prec == "fp64":
+        assert abs(lz[0] - o_lz) < 1e-10 * abs(o_lz)
+        sp = sp.cpu().numpy().reshape(L, L + 1, CHI)
+        checked = 0
+        for r in range(0, L, 4):
+            for c in range(1, L):
+                o_s, gap = rows[r].spectra[c - 1], rows[r].cut_gap[c - 1]
+                if gap > 1e-6:
+                    keep = o_s > 1e-7
+                    np.testing.assert_allclose(sp[r, c, :keep.sum()], o_s[keep], rtol=1e-8, atol=1e-12)
+                    checked += 1
+        assert checked > 100
+        spins = parity.split_spins(props.spins.cpu().numpy(), list(Ls), S)
+        _, nbd = parity.compare_proposals(rows, Jh, Jv, beta, 42, 0, 0, spins[0],
+                                          props.logq.cpu().numpy()[0], props.E.cpu().numpy()[0])
+        assert nbd <= 1
+    else:
+        assert abs(lz[0] - o_lz) / (L * L) < 1e-6, (lz[0], o_lz)
+        _audit(t, list(Ls), reals, envs, beta, S, props)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_chi64_beta3_L64(P, prec):
+    """beta = 3 at chi = 64, L = 64 (cutoff-limited bonds up to 56): the float64 build
+    follows the oracle row by row; float64 proposals are bit-exact up to boundary draws.
+    Spectra to 2e-7 absolute (normalised to the largest value), as the beta = 3
+    conditioning allows."""
+    Ls, beta, S = (64,), 3.0, 64
+    t, lz, props, (_, sp, ri), st, flags = _gpu(P, Ls, beta, prec, "pmj", S, diag=True)
+    if prec == "fp64":
+        assert st == 0 and not flags.any()
+    reals, envs = _oracle(Ls, beta, "pmj", t.cutoff)
+    (Jh, Jv), rows, L = reals[0], envs[0], Ls[0]
+    ri = ri.cpu().numpy().reshape(-1, 14)
+    for r in range(L):
+        assert abs(ri[r, 0] - rows[r].log_scale) < 1e-9 * abs(rows[r].log_scale), r
+    assert abs(lz[0] - bmps.log_z(rows)) < 1e-9 * abs(lz[0])
+    sp = sp.cpu().numpy().reshape(L, L + 1, CHI)
+    for r in range(0, L, 8):
+        for c in range(1, L):
+            o_s = rows[r].spectra[c - 1]
+            np.testing.assert_allclose(sp[r, c, :o_s.size], o_s, rtol=0, atol=2e-7)
+    if prec == "fp64":
+        spins = parity.split_spins(props.spins.cpu().numpy(), list(Ls), S)
+        _, nbd = parity.compare_proposals(rows, Jh, Jv, beta, 42, 0, 0, spins[0],
+                                          props.logq.cpu().numpy()[0], props.E.cpu().numpy()[0])
+        assert nbd <= 1
+
+
+def test_shard_handle_reproduces_full_handle(P):
+    """A handle over a shard of the realizations, named by their global indices, draws what
+    the handle over the whole set draws for them (bit for bit): the per-realization results
+    do not depend on how the set is split over processes."""
+    from paper_2509_19006_b300 import shard
+    Ls, chi, beta, S = [9, 6, 12, 7, 10], 8, 1.2, 32
+    reals = parity.realizations(Ls, "gauss")
+    full = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    full.build_envs(torch.from_numpy(parity.packed_J(reals)).cuda())
+    st_f = full.mh_init(5)
+    pf = full.propose(S, 42, 100)
+    full.mh_step(pf, st_f, 42)
+    lz_f = full.log_z().cpu().numpy()
+    spins_f = parity.split_spins(pf.spins.cpu().numpy(), Ls, S)
+    for ids in shard.lpt_partition(Ls, chi, 2):
+        sub = P.TNMC([Ls[g] for g in ids], chi, beta, "fp64", max_samples=S)
+        sub.set_realization_ids(ids)
+        sub.build_envs(torch.from_numpy(parity.packed_J([reals[g] for g in ids])).cuda())
+        st_s = sub.mh_init(5)
+        ps = sub.propose(S, 42, 100)
+        sub.mh_step(ps, st_s, 42)
+        spins_s = parity.split_spins(ps.spins.cpu().numpy(), [Ls[g] for g in ids], S)
+        for k, g in enumerate(ids):
+            np.testing.assert_array_equal(spins_s[k], spins_f[g])
+            assert ps.logq.cpu().numpy()[k].tolist() == pf.logq.cpu().numpy()[g].tolist()
+            assert sub.log_z().cpu().numpy()[k] == lz_f[g]
+            assert st_s.n_accept.cpu().numpy()[k] == st_f.n_accept.cpu().numpy()[g]
+            assert st_s.logq.cpu().numpy()[k] == st_f.logq.cpu().numpy()[g]

@@ -78,3 +78,35 @@ def test_step_captured_in_a_cuda_graph(P, prec):
         assert torch.equal(a, b)
     status, flags = t.device_status()
     assert status == 0 and not flags.any()
+
+
+def test_handle_on_side_stream_orders_with_the_callers_stream(P):
+    """A handle on its own stream, called from the default stream without a stream
+    context: the couplings written on the default stream (after a long kernel) are
+    complete before the build reads them, and the outputs are complete before the
+    default stream reads them."""
+    Ls, chi, beta, S = [12, 9], 8, 1.3, 48
+    reals = parity.realizations(Ls, "pmj")
+    Jh = torch.from_numpy(parity.packed_J(reals))
+    ref = P.TNMC(Ls, chi, beta, "fp64", max_samples=S)
+    ref.build_envs(Jh.cuda())
+    want_lz = ref.log_z().cpu()
+    want = ref.propose(S, 42, 0)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=S, stream=side)
+    for k in range(3):
+        J = torch.zeros_like(Jh, device="cuda")
+        big = torch.randn(4096, 4096, device="cuda")
+        for _ in range(8):
+            big = big @ big / 64.0            # keep the default stream busy
+        J.copy_(Jh, non_blocking=False)
+        J += big[0, 0] * 0.0                  # the couplings depend on the long kernel chain
+        t.build_envs(J)
+        lz = t.log_z()
+        props = t.propose(S, 42, 0)
+        got_lz = lz.clone()                   # default-stream reads of the outputs
+        got_spins = props.spins.clone()
+        torch.cuda.synchronize()
+        assert torch.equal(got_lz.cpu(), want_lz), k
+        assert torch.equal(got_spins, want.spins), k

@@ -114,6 +114,31 @@ def test_adam_first_step_is_signed_learning_rate():
     np.testing.assert_allclose(th, [-0.01, 0.01, -0.01, 0.0], rtol=1e-8)
 
 
+def test_adam_two_steps_hand_computed():
+    """Two Adam steps worked by hand with b1 = 1/2, b2 = 3/4, lr = 1/10, eps = 0.
+
+    Coordinate A, gradients 1 then 3: m = 1/2, v = 1/4 after step 1 (update -lr);
+    after step 2 m = 1/4 + 3/2 = 7/4, v = 3/16 + 9/4 = 39/16, bias-corrected
+    m^ = (7/4)/(3/4) = 7/3 and v^ = (39/16)/(7/16) = 39/7.
+    Coordinate B, gradients -2 then 1/2: m = -1, v = 1 after step 1 (update +lr);
+    then m = -1/2 + 1/4 = -1/4, v = 3/4 + 1/16 = 13/16, m^ = -1/3, v^ = 13/7.
+    Step 1 alone cannot tell b1 from b2 (the bias correction cancels both); step 2
+    can: with the two swapped the same formulas give other numbers.
+    """
+    lr, b1, b2 = 0.1, 0.5, 0.75
+    g1, g2 = np.array([1.0, -2.0]), np.array([3.0, 0.5])
+    th, m, v = learned.adam(np.zeros(2), g1, np.zeros(2), np.zeros(2), 1, lr, b1, b2, eps=0.0)
+    np.testing.assert_allclose(th, [-0.1, 0.1], rtol=1e-15)
+    th, m, v = learned.adam(th, g2, m, v, 2, lr, b1, b2, eps=0.0)
+    want = [-0.1 - 0.1 * (7 / 3) / np.sqrt(39 / 7), 0.1 + 0.1 * (1 / 3) / np.sqrt(13 / 7)]
+    np.testing.assert_allclose(th, want, rtol=1e-14)
+    np.testing.assert_allclose(m, [7 / 4, -1 / 4], rtol=1e-15)
+    np.testing.assert_allclose(v, [39 / 16, 13 / 16], rtol=1e-15)
+    th_s, m_s, v_s = learned.adam(np.zeros(2), g1, np.zeros(2), np.zeros(2), 1, lr, b2, b1, eps=0.0)
+    th_s, _, _ = learned.adam(th_s, g2, m_s, v_s, 2, lr, b2, b1, eps=0.0)
+    assert np.abs(th_s - np.array(want)).max() > 1e-3
+
+
 def test_training_reaches_teacher_entropy_floor():
     """Targets drawn from a teacher network of the same form: Adam drives the loss to its floor."""
     rng = np.random.default_rng(4)
