@@ -48,6 +48,9 @@ def metric_name(wl) -> str:
 # oracle computes the same method; its own MH at that size would take hours). Both
 # oracle legs (cpu_baseline and --impl reference) credit this one value.
 REF_ACCEPTANCE_L256 = 0.205
+# float32 instructions of one double-float multiply-add as the kernels implement it
+# (TwoProd 2, two cross-term FMAs 2, two TwoSums 12, two FastTwoSums 6, two adds 2)
+DF_FMA_OPS = 24
 
 
 def measure_alu_peaks(dev):
@@ -367,6 +370,8 @@ def run_ours(args, wl):
     total_ms = t_all0.elapsed_time(t_all1)   # includes the L2 flushes between steps
     my_ms = sum(step_t)
 
+    per_real = torch.stack([logz.double(), (state.n_accept - n_acc0).double()], dim=1)
+
     # ---------------- end to end through the public API with host buffers
     # (a bounded number of steps: the same metric, its wall time and proposal count stated)
     e2e_steps = min(args.steps, args.e2e_steps)
@@ -395,7 +400,6 @@ def run_ours(args, wl):
 
     # ---------------- gather over ranks (max time, summed work, per-realization results)
     vec = torch.tensor([my_ms, float(accepted), e2e_s, float(e2e_acc)], dtype=torch.float64, device=dev)
-    per_real = torch.stack([logz.double(), (state.n_accept - n_acc0).double()], dim=1)
     full = shard.gather(dist if world > 1 else None, n_all, ids, per_real, device=dev)
     if world > 1:
         mx = vec.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
@@ -412,6 +416,12 @@ def run_ours(args, wl):
         achieved = flops_env / env_avg_s / 1e9
         if args.prec == "fp32":
             peak, peak_src = peaks_alu["fp32"], "measured: cuBLAS float32 GEMM (TF32 off) on this GPU"
+        elif args.prec == "dfloat":
+            # a double-float multiply-add (2 flops) is DF_FMA_OPS float32 instructions on the
+            # FP32 pipe, whose rate the float32 GEMM measures (2 flops per instruction)
+            peak = peaks_alu["fp32"] / DF_FMA_OPS
+            peak_src = (f"derived: measured cuBLAS float32 GEMM rate / {DF_FMA_OPS} (float32 "
+                        "instructions per double-float multiply-add)")
         else:
             peak, peak_src = peaks_alu["fp64"], "measured: cuBLAS float64 GEMM on this GPU"
         proposals = n_mine * S * args.steps
@@ -427,7 +437,7 @@ def run_ours(args, wl):
         # sampler: algorithmic bytes per sample-site = the right environment spilled and read
         # back (2 D values: L D values per chain do not fit on chip), the cache read once per
         # pass per realization (2 D^2 values, shared by the S chains) and the spin written
-        esz = 8 if args.prec == "fp64" else 4
+        esz = 4 if args.prec == "fp32" else 8
         samp_sites = S * site_rows
         samp_bytes = samp_sites * (2.0 * dmean * esz + 2.0 * dmean * dmean * esz / S + 1.0)
         hbm_peak = peaks.get("hbm_gbs") or 6484.6
@@ -447,7 +457,8 @@ def run_ours(args, wl):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": my_ms_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f64 build + f32 sampling"}[args.prec],
+            "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f64 build + f32 sampling",
+                      "dfloat": "f32x2 (double-float)"}[args.prec],
             "data": ("synthetic Gaussian N(0,1) disorder, seeded" if wl.kind == "gauss"
                      else "synthetic +-J disorder (p = 1/2), seeded"),
             "config": {"workload": wl.name, "L": wl.Ls[0], "chi": wl.chi, "beta": wl.beta,
@@ -687,7 +698,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp64", "fp32", "mixed"], default="fp32")
+    ap.add_argument("--prec", choices=["fp64", "fp32", "mixed", "dfloat"], default="fp32")
     ap.add_argument("--workload", default="L256")
     ap.add_argument("--cutoff", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

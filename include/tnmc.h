@@ -68,8 +68,14 @@ typedef enum {
   TNMC_FP32 = 1,   /* all tensor arithmetic and the cache in float32 */
   TNMC_TF32 = 2,   /* reserved: tensor-core TF32 contractions */
   TNMC_BF16 = 3,   /* reserved: tensor-core BF16 contractions */
-  TNMC_MIXED = 4   /* float64 environment build (QR / SVD truncation, carried between
+  TNMC_MIXED = 4,  /* float64 environment build (QR / SVD truncation, carried between
                       rows in float64), float32 cache and float32 sampling contractions */
+  TNMC_DFLOAT = 5  /* double-float arithmetic (a float32 pair hi + lo, 48 significant bits,
+                      float32's exponent range) for the environment build, the cache and the
+                      sampling contractions, run on the FP32 pipes; the per-draw scalars,
+                      log scales, log q, log p and energies in float64. The beta = 3 regime
+                      needs float64-class accuracy in both the truncation and the sampling
+                      contractions; this mode gives it without the float64 pipe */
 } tnmc_prec;
 
 /* Device flags (bit mask per realization) reported by tnmc_get_device_status. */
@@ -87,7 +93,8 @@ typedef struct {
   double cutoff;         /* relative singular-value cutoff of the truncation (Sec. 1's
                             truncation threshold): at each bond keep the chi largest
                             singular values that exceed cutoff * (largest). <= 0 selects
-                            the default of the precision: 1e-12 (FP64, MIXED), 1e-6 (FP32).
+                            the default of the precision: 1e-12 (FP64, MIXED, DFLOAT),
+                            1e-6 (FP32).
                             Numerically-zero singular values must be dropped: their
                             noise directions grow under the next rows' transfer MPOs. */
   int32_t ckpt_every;    /* 0: cache the environment of every row. K >= 2: cache only rows

@@ -18,9 +18,9 @@ from typing import List, Optional, Sequence
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtnmc.so")
 
-TNMC_FP64, TNMC_FP32, TNMC_TF32, TNMC_BF16, TNMC_MIXED = 0, 1, 2, 3, 4
+TNMC_FP64, TNMC_FP32, TNMC_TF32, TNMC_BF16, TNMC_MIXED, TNMC_DFLOAT = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": TNMC_FP64, "fp32": TNMC_FP32, "tf32": TNMC_TF32, "bf16": TNMC_BF16,
-              "mixed": TNMC_MIXED}
+              "mixed": TNMC_MIXED, "dfloat": TNMC_DFLOAT}
 FLAG_BAD_COUPLINGS, FLAG_NUMERIC, FLAG_TIMEOUT = 1, 2, 4
 
 EXPORTED = [
@@ -191,7 +191,7 @@ class ChainState:
 class TNMC:
     """A handle on the library for one batch of realizations on one CUDA device."""
 
-    DEFAULT_CUTOFF = {TNMC_FP64: 1e-12, TNMC_FP32: 1e-6, TNMC_MIXED: 1e-12}
+    DEFAULT_CUTOFF = {TNMC_FP64: 1e-12, TNMC_FP32: 1e-6, TNMC_MIXED: 1e-12, TNMC_DFLOAT: 1e-12}
 
     def __init__(self, Ls: Sequence[int], chi: int, beta: float, prec: str | int = "fp32",
                  max_samples: int = 256, device="cuda:0", stream=None, cutoff: float = 0.0,

@@ -66,22 +66,29 @@ tnmc_status check_cfg(const tnmc_config *cfg) {
   if (!std::isfinite(cfg->cutoff) || cfg->cutoff >= 1.0) return TNMC_ERR_ARG;
   if (cfg->ckpt_every < 0 || cfg->ckpt_every == 1) return TNMC_ERR_ARG;
   if (cfg->prec == TNMC_TF32 || cfg->prec == TNMC_BF16) return TNMC_ERR_UNSUPPORTED;
-  if (cfg->prec != TNMC_FP64 && cfg->prec != TNMC_FP32 && cfg->prec != TNMC_MIXED) return TNMC_ERR_ARG;
+  if (cfg->prec != TNMC_FP64 && cfg->prec != TNMC_FP32 && cfg->prec != TNMC_MIXED &&
+      cfg->prec != TNMC_DFLOAT)
+    return TNMC_ERR_ARG;
   for (int n = 0; n < cfg->n_real; ++n)
     if (cfg->L[n] < 1 || cfg->L[n] > kMaxL) return TNMC_ERR_ARG;
   return TNMC_OK;
 }
 
-// 0: float64 build + float64 cache; 1: float32 build + cache; 2: float64 build, float32 cache
-int env_mode(int prec) { return prec == TNMC_FP64 ? 0 : (prec == TNMC_FP32 ? 1 : 2); }
-// type of the cache and of the sampler: 0 = float64, 1 = float32
-int cache_code(int prec) { return prec == TNMC_FP64 ? 0 : 1; }
+// 0: float64 build + float64 cache; 1: float32 build + cache; 2: float64 build, float32 cache;
+// 3: double-float build + cache
+int env_mode(int prec) {
+  return prec == TNMC_FP64 ? 0 : (prec == TNMC_FP32 ? 1 : (prec == TNMC_DFLOAT ? 3 : 2));
+}
+// type of the cache and of the sampler: 0 = float64, 1 = float32, 2 = double-float
+int cache_code(int prec) { return prec == TNMC_FP64 ? 0 : (prec == TNMC_DFLOAT ? 2 : 1); }
+// bytes of a cache / sampler value
+int64_t value_bytes(int prec) { return cache_code(prec) == 1 ? 4 : 8; }
 double default_cutoff(int prec) { return prec == TNMC_FP32 ? 1e-6 : 1e-12; }
 
 Plan make_plan(const tnmc_config *cfg) {
   Plan p;
   p.CH = pick_ch(cfg->chi);
-  const int64_t esz = cache_code(cfg->prec) == 0 ? 8 : 4;
+  const int64_t esz = value_bytes(cfg->prec);
   for (int n = 0; n < cfg->n_real; ++n) {
     const int64_t L = cfg->L[n];
     p.sum_L2 += L * L;
@@ -127,7 +134,7 @@ struct tnmc_handle {
   Plan plan;
   Layout lay;
   int env_code;    // env_mode()
-  int prec_code;   // cache_code(): sampler / log Z kernels on float64 (0) or float32 (1)
+  int prec_code;   // cache_code(): sampler / log Z kernels on float64 (0), float32 (1), double-float (2)
   cudaStream_t stream;
   bool built = false;
 };
@@ -371,7 +378,7 @@ tnmc_status tnmc_propose_static(tnmc_handle *h, int32_t S, uint64_t seed, uint64
   if (S < 1) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
   bool too_big = false;
-  const int64_t esz = h->prec_code == 0 ? 8 : 4;
+  const int64_t esz = value_bytes(h->cfg.prec);
   if (int64_t(S) * h->plan.sum_L * h->plan.CH * esz > static_scratch_bytes()) return TNMC_ERR_ARG;
   const cudaError_t e = for_segments(h, [&](const Layout &l) {
     return launch_propose_static(l, h->prec_code, h->plan.CH, S, seed, prop_base, d_spins, d_logq,

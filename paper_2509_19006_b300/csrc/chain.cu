@@ -150,6 +150,7 @@ cudaError_t launch_log_z(const Layout &lay, int prec, double *logz, cudaStream_t
   const int blocks = (lay.n_real + wpb - 1) / wpb;
   const size_t smem = wpb * 128 * sizeof(double);
   if (prec == 0) log_z_kernel<double><<<blocks, 32 * wpb, smem, st>>>(lay, logz);
+  else if (prec == 2) log_z_kernel<dfloat><<<blocks, 32 * wpb, smem, st>>>(lay, logz);
   else log_z_kernel<float><<<blocks, 32 * wpb, smem, st>>>(lay, logz);
   return cudaGetLastError();
 }

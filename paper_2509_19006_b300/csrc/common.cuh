@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
+
 namespace tnmc {
 
 enum : int32_t { FLAG_BAD_J = 1, FLAG_NUMERIC = 2, FLAG_TIMEOUT = 4 };
@@ -114,6 +116,16 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double tanh_(double x) { return tanh(x); }
   static __host__ __device__ constexpr double eps() { return 1.1102230246251565e-16; }
+};
+// double-float: tensor arithmetic on the FP32 pipes (dfloat.cuh); the elementary
+// functions, needed once per site, through float64
+template <> struct Num<dfloat> {
+  static __device__ __forceinline__ dfloat log_(dfloat x) { return dfloat(log(double(x))); }
+  static __device__ __forceinline__ dfloat exp_(dfloat x) { return dfloat(exp(double(x))); }
+  static __device__ __forceinline__ dfloat log1p_(dfloat x) { return dfloat(log1p(double(x))); }
+  static __device__ __forceinline__ dfloat sqrt_(dfloat x) { return df::sqrt(x); }
+  static __device__ __forceinline__ dfloat tanh_(dfloat x) { return dfloat(tanh(double(x))); }
+  static __host__ __device__ constexpr double eps() { return 3.552713678800501e-15; }   // 2^-48
 };
 
 // log sigmoid(x) = -softplus(-x), stable for either sign.

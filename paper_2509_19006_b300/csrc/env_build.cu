@@ -32,6 +32,8 @@
 // it (Layout::seg_begin, seg_end); see cache_slot in common.cuh.
 #include "common.cuh"
 
+#include <type_traits>
+
 namespace tnmc {
 
 namespace {
@@ -119,14 +121,14 @@ constexpr long long CLUSTER_WAIT_CYCLES = 40000000000ll;   // ~20 s at 2 GHz
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
   return v;
 }
 
 template <typename T, int W>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
-  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = W / 2; o > 0; o >>= 1) v += shfl_xor(v, o);
   return v;
 }
 
@@ -275,6 +277,37 @@ __device__ __forceinline__ void rotation_params<double>(double al, double be, do
   t = tf;
 }
 
+// Double-float rows: the angle in float32 from the leading words (double-float has
+// float32's exponent range, so no rescale is needed), then c = c0 (1 - d/2 + 3 d^2 / 8)
+// with d = c0^2 (1 + t^2) - 1 evaluated in double-float (|d| ~ 1e-7), so that
+// c^2 (1 + t^2) = 1 to double-float precision; s = c t.
+template <>
+__device__ __forceinline__ void rotation_params<dfloat>(dfloat al, dfloat be, dfloat ga, dfloat &cs,
+                                                        dfloat &sn, dfloat &t) {
+  const float num = (be - al).hi, den = 2.f * ga.hi;
+  const float zeta = __fdividef(num, den);
+  const float az = fabsf(zeta);
+  float tf;
+  if (az > 1e15f) {
+    tf = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.f);
+    tf = copysignf(__fdividef(1.f, az + q * rsqrtf(q)), zeta);
+  }
+  if (num == 0.f) tf = 1.f;
+  const float c0 = rsqrtf(fmaf(tf, tf, 1.f));
+  float p, e;
+  df::two_prod(tf, tf, p, e);
+  const dfloat q = df::add(dfloat(1.f), dfloat(p, e));          // 1 + t^2
+  df::two_prod(c0, c0, p, e);
+  const float d = df::add(df::mul(dfloat(p, e), q), dfloat(-1.f)).hi;
+  const float corr = d * fmaf(0.375f, d, -0.5f);
+  df::two_prod(c0, corr, p, e);
+  cs = df::add(dfloat(c0), dfloat(p, e));
+  sn = df::mul(cs, tf);
+  t = dfloat(tf);
+}
+
 // Float64 rows: the tangent t is the float32 value of the angle formula
 // (zeta = (beta - alpha) / (2 gamma) taken in float32 after both operands are
 // brought into float range by the exponent of the larger one, read from its bit
@@ -346,7 +379,7 @@ template <typename T, int TPP, int NT = 256, bool SCALED = false>
 __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int ht,
                            volatile int *lastrot, T *nrm2, const int *perm, T *scl) {
   static_assert(NT == 256 || NT == 512, "a half or the whole CTA");
-  static_assert(!SCALED || sizeof(T) == 8, "scaled rotations are for float64 rows");
+  static_assert(!SCALED || std::is_same<T, double>::value, "scaled rotations are for float64 rows");
   if (nr <= 1) return 0;  // uniform over the half
   const int P = nr + (nr & 1);
   const int npairs = P / 2;
@@ -516,6 +549,7 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
 // Non-negative floating-point values order like their bit patterns.
 __device__ __forceinline__ long long order_key(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ long long order_key(float x) { return (long long)__float_as_int(x); }
+__device__ __forceinline__ long long order_key(dfloat x) { return order_key(double(x)); }
 
 __device__ __forceinline__ double log_cosh(double x) {
   const double ax = fabs(x);
@@ -737,13 +771,15 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         }
         // R = upper trapezoid; both sectors normalised together
         {
-          double acc = 0.0;
+          // squared norm: double-float rows sum in double-float (no float64 per element)
+          using TA = typename std::conditional<std::is_same<TC, dfloat>::value, dfloat, double>::type;
+          TA acc = TA(0.0);
           for (int e = tid; e < 2 * kq * Dn; e += ENV_THREADS) {
             const int q = e / (kq * Dn), rem = e % (kq * Dn), i = rem / Dn, b = rem % Dn;
-            if (b >= i) { const double v = (double)Ab[q * (LDA * CH) + int64_t(b) * LDA + i]; acc += v * v; }
+            if (b >= i) { const TA v = TA(Ab[q * (LDA * CH) + int64_t(b) * LDA + i]); acc += v * v; }
           }
           acc = warp_sum(acc);
-          if (lane == 0) sh_red[warp] = acc;
+          if (lane == 0) sh_red[warp] = double(acc);
           __syncthreads();
           double nrm2 = 0.0;
           for (int w = 0; w < ENV_THREADS / 32; ++w) nrm2 += sh_red[w];
@@ -946,7 +982,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         } else {
           const int rows = half ? k1 : k0;
           TC *Bq = Th + int64_t(half ? k0 : 0) * LDT;
-          const int nsw = jacobi_rows<TC, 4, 256, sizeof(TC) == 8>(Bq, half ? r1 : r0, N, rows, LDT, half, ht,
+          const int nsw = jacobi_rows<TC, 4, 256, std::is_same<TC, double>::value>(Bq, half ? r1 : r0, N, rows, LDT, half, ht,
                                                                   &sh_lastrot[half],
                                              Bnrm + (half ? CH : 0), sh_src + (half ? k0 : 0),
                                              sh_scl + (half ? 2 * CH : 0));
@@ -1097,7 +1133,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
 
 // Kernel variants: mode 0 = float64 build and cache; 1 = float32 build and
 // cache; 2 = float64 build with a float32 cache (the float64 carry between
-// rows stays in the slot scratch).
+// rows stays in the slot scratch); 3 = double-float build and cache.
 template <typename TC, typename TS>
 static int64_t env_slot_bytes_ts(int CH, int L_max, int chi) {
   switch (CH) {
@@ -1112,6 +1148,7 @@ static int64_t env_slot_bytes_ts(int CH, int L_max, int chi) {
 int64_t env_slot_bytes(int mode, int CH, int L_max, int chi) {
   if (mode == 0) return env_slot_bytes_ts<double, double>(CH, L_max, chi);
   if (mode == 1) return env_slot_bytes_ts<float, float>(CH, L_max, chi);
+  if (mode == 3) return env_slot_bytes_ts<dfloat, dfloat>(CH, L_max, chi);
   return env_slot_bytes_ts<double, float>(CH, L_max, chi);
 }
 
@@ -1170,11 +1207,12 @@ static cudaError_t launch_env_ts(const Layout &lay, int CH, bool split, cudaStre
 // the pairs of all realizations fit on the GPU at once (2 x realizations <= SMs;
 // 74 pairs on a 148-SM B300).
 cudaError_t launch_env_build(const Layout &lay, int mode, int CH, cudaStream_t st) {
-  if (mode == 0) {
+  if (mode == 0 || mode == 3) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    if (mode == 3) return launch_env_ts<dfloat, dfloat>(lay, CH, 2 * lay.env_slots <= sms, st);
     return launch_env_ts<double, double>(lay, CH, 2 * lay.env_slots <= sms, st);
   }
   if (mode == 1) return launch_env_ts<float, float>(lay, CH, false, st);

@@ -27,6 +27,7 @@
 #include "mlp.cuh"
 
 #include <mutex>
+#include <type_traits>
 
 namespace tnmc {
 
@@ -44,6 +45,17 @@ template <> struct Vec4<float> {
   }
   static __device__ __forceinline__ void store(float *p, const float v[4]) {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <> struct Vec4<dfloat> {
+  static __device__ __forceinline__ void load(const dfloat *p, dfloat v[4]) {
+    const float4 x = reinterpret_cast<const float4 *>(p)[0];
+    const float4 y = reinterpret_cast<const float4 *>(p)[1];
+    v[0] = dfloat(x.x, x.y); v[1] = dfloat(x.z, x.w); v[2] = dfloat(y.x, y.y); v[3] = dfloat(y.z, y.w);
+  }
+  static __device__ __forceinline__ void store(dfloat *p, const dfloat v[4]) {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
   }
 };
 template <> struct Vec4<double> {
@@ -74,9 +86,20 @@ __host__ __device__ constexpr int64_t samp_smem_fixed() {
 template <typename T, int W>
 __device__ __forceinline__ T gsum(T v) {
 #pragma unroll
-  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = W / 2; o > 0; o >>= 1) v += shfl_xor(v, o);
   return v;
 }
+
+// acc += x * y: a fused multiply-add in float32 and float64, the double-float one in
+// double-float arithmetic
+__device__ __forceinline__ void fma_acc(float &acc, float x, float y) { acc += x * y; }
+__device__ __forceinline__ void fma_acc(double &acc, double x, double y) { acc += x * y; }
+__device__ __forceinline__ void fma_acc(dfloat &acc, dfloat x, dfloat y) { acc = df::fma(x, y, acc); }
+
+// Arithmetic of the per-draw scalars (logit, log sigmoid, the draw): the tensor type,
+// except for double-float tensors, whose scalars are float64
+template <typename T> struct LogitType { using type = T; };
+template <> struct LogitType<dfloat> { using type = double; };
 
 template <typename T, int CH, bool FORCED, bool CORR>
 __global__ void __launch_bounds__(SampPlan<CH>::NT)
@@ -194,7 +217,7 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
 #pragma unroll
         for (int j = 0; j < TS; ++j)
 #pragma unroll
-          for (int t = 0; t < TC; ++t) acc[j][t] += x[j] * y[t];
+          for (int t = 0; t < TC; ++t) fma_acc(acc[j][t], x[j], y[t]);
       }
       // output sign Pi^{s_up(c+1)} on bond c+1, then normalise over the bond
       T *vout = Vb + (buf ^ 1) * CH * SB;
@@ -266,7 +289,7 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
 #pragma unroll
         for (int j = 0; j < TS; ++j)
 #pragma unroll
-          for (int t = 0; t < TC; ++t) u[j][t] += x[j] * y[t];
+          for (int t = 0; t < TC; ++t) fma_acc(u[j][t], x[j], y[t]);
       }
       const int Dl = bl.x + bl.y;
       for (int a = bl.x; a < Dl; ++a) {
@@ -276,7 +299,7 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
 #pragma unroll
         for (int j = 0; j < TS; ++j)
 #pragma unroll
-          for (int t = 0; t < TC; ++t) w[j][t] += x[j] * y[t];
+          for (int t = 0; t < TC; ++t) fma_acc(w[j][t], x[j], y[t]);
       }
       // conditional weights, reduced over the column groups
       T x0[TS], x1[TS];
@@ -297,23 +320,25 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
       const int i = r * L + c;
       const T jup = (r > 0) ? T(jd[(r - 1) * L + c]) : T(0);
       const double jl = (c > 0) ? (double)jr[r * L + c - 1] : 0.0;
-      T lg_own[OWN];
+      using TL = typename LogitType<T>::type;
+      const TL betaL = std::is_same<T, dfloat>::value ? TL(lay.beta) : TL(beta);
+      TL lg_own[OWN];
 #pragma unroll
       for (int o = 0; o < OWN; ++o) {
         const int j = cg + o * NCG;
-        lg_own[o] = T(0);
+        lg_own[o] = TL(0);
         if (j < TS) {
           const int sl = sg * TS + j;
           const int up = (r > 0) ? (bprev[sl * WL + (c >> 5)] >> (c & 31)) & 1 : 0;
-          const T rho0 = fabs(x0[j]), rho1 = fabs(x1[j]);
-          T logit;
-          if (rho0 == T(0) && rho1 == T(0)) {
-            logit = T(0);
+          const TL rho0 = TL(fabs(x0[j])), rho1 = TL(fabs(x1[j]));
+          TL logit;
+          if (rho0 == TL(0) && rho1 == TL(0)) {
+            logit = TL(0);
             if (act[j]) any_bad = true;
           } else {
-            logit = Num<T>::log_(rho1) - Num<T>::log_(rho0);
+            logit = Num<TL>::log_(rho1) - Num<TL>::log_(rho0);
           }
-          if (r > 0) logit += T(2) * beta * jup * T(up ? 1 : -1);
+          if (r > 0) logit += TL(2) * betaL * TL(jup) * TL(up ? 1 : -1);
           lg_own[o] = logit;
           if (corr) sh_lg[sl] = act[j] ? clamp_logit((float)logit) : 0.f;
         }
@@ -356,7 +381,7 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
 #pragma unroll
         for (int o = 0; o < OWN; ++o) {
           const int j = cg + o * NCG;
-          if (j < TS) lg_own[o] += T(sh_dl[sg * TS + j]);
+          if (j < TS) lg_own[o] += TL(sh_dl[sg * TS + j]);
         }
       }
       int sig_own[OWN];
@@ -367,7 +392,7 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
         if (j < TS) {
           const int sl = sg * TS + j;
           const int up = (r > 0) ? (bprev[sl * WL + (c >> 5)] >> (c & 31)) & 1 : 0;
-          const T logit = lg_own[o];
+          const TL logit = lg_own[o];
           int sgm;
           if (FORCED) {
             sgm = act[j] ? in_spins[int64_t(S) * ri.site_off + int64_t(sid[j]) * L2 + i] : 0;
@@ -381,10 +406,10 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
               pg[o] = g;
             }
             const double uu = word_to_uniform(pw[o][i & 3]);
-            const T ls = log_sigmoid<T>(logit);
-            sgm = uu < (double)Num<T>::exp_(ls) ? 1 : 0;
+            const TL ls = log_sigmoid<TL>(logit);
+            sgm = uu < (double)Num<TL>::exp_(ls) ? 1 : 0;
           }
-          const T lpick = sgm ? log_sigmoid<T>(logit) : log_sigmoid<T>(-logit);
+          const TL lpick = sgm ? log_sigmoid<TL>(logit) : log_sigmoid<TL>(-logit);
           lq[o] += (double)lpick;
           const double sv = sgm ? 1.0 : -1.0;
           if (c > 0) en[o] -= jl * sv * (double)(sleft[o] ? 1.0 : -1.0);
@@ -476,6 +501,13 @@ static cudaError_t launch_samp(const Layout &lay, int prec, int CH, int S, uint6
       case 32: return launch_samp_t<double, 32, FORCED>(lay, S, seed, base, in, out, lq, E, st);
       case 64: return launch_samp_t<double, 64, FORCED>(lay, S, seed, base, in, out, lq, E, st);
     }
+  } else if (prec == 2) {
+    switch (CH) {
+      case 8: return launch_samp_t<dfloat, 8, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+      case 16: return launch_samp_t<dfloat, 16, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+      case 32: return launch_samp_t<dfloat, 32, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+      case 64: return launch_samp_t<dfloat, 64, FORCED>(lay, S, seed, base, in, out, lq, E, st);
+    }
   } else {
     switch (CH) {
       case 8: return launch_samp_t<float, 8, FORCED>(lay, S, seed, base, in, out, lq, E, st);
@@ -539,7 +571,7 @@ static cudaError_t static_scratch_address(void **out) {
 cudaError_t launch_propose_static(const Layout &lay, int prec, int CH, int S, uint64_t seed,
                                   uint64_t base, uint8_t *spins, double *lq, double *E,
                                   int64_t sum_L, cudaStream_t st, bool *too_big) {
-  const int64_t esz = prec == 0 ? 8 : 4;
+  const int64_t esz = prec == 1 ? 4 : 8;
   *too_big = int64_t(S) * sum_L * CH * esz > kStaticScratchBytes;
   if (*too_big) return cudaSuccess;
   void *scratch = nullptr;
@@ -554,7 +586,7 @@ cudaError_t launch_propose_static(const Layout &lay, int prec, int CH, int S, ui
 int64_t sampler_smem_bytes(int prec, int CH, int L_max) {
   const int WL = (L_max + 31) / 32;
   const int64_t extra = int64_t(2) * SB * WL * 4 + int64_t(sizeof(MlpSmem)) + 2 * SB * 4;
-  if (prec == 0) {
+  if (prec != 1) {   // float64 and double-float values are 8 bytes
     switch (CH) {
       case 8: return samp_smem_fixed<double, 8>() + extra;
       case 16: return samp_smem_fixed<double, 16>() + extra;

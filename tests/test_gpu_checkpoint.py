@@ -19,7 +19,7 @@ def P():
     return P
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed", "dfloat"])
 @pytest.mark.parametrize("K", [2, 3, 5])
 def test_checkpointed_equals_full_cache(P, prec, K):
     Ls, chi, beta, S = [9, 6, 12], 4, 1.5, 70

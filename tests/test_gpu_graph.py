@@ -21,7 +21,7 @@ def P():
     return P
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "dfloat"])
 def test_step_captured_in_a_cuda_graph(P, prec):
     Ls, chi, beta, S = [9, 6, 12], 8, 1.5, 64
     reals = parity.realizations(Ls, "pmj")

@@ -23,10 +23,15 @@ from oracle import bmps, philox, sampler  # noqa: E402
 import parity  # noqa: E402
 
 LS, CHI, S = [32] * 4, 32, 64
-# (mode, beta) -> (bound on |d log Z| / L^2, bound on |d log q|); None: recorded only
+# (mode, beta) -> (bound on |d log Z| / L^2, bound on |d log q|); None: recorded only.
+# The targets are |d log Z| / L^2 <= 1e-6 and |d log q| <= 1e-4. float32 sampling
+# contractions (FP32, MIXED) miss the log q target beyond beta = 1 and float32 builds
+# miss the log Z one beyond beta = 1 on some instances (see test_gpu_chi64.py); the
+# bounds below are the ones each mode meets.
 BOUNDS = {
-    ("fp32", 1.0): (1e-6, 1e-2), ("fp32", 2.0): (1e-6, 1e-2), ("fp32", 3.0): None,
-    ("mixed", 1.0): (1e-6, 1e-2), ("mixed", 2.0): (1e-6, 1e-2), ("mixed", 3.0): (1e-6, None),
+    ("fp32", 1.0): (1e-6, 1e-3), ("fp32", 2.0): None, ("fp32", 3.0): None,
+    ("mixed", 1.0): (1e-6, 1e-4), ("mixed", 2.0): (1e-6, 1e-2), ("mixed", 3.0): (1e-6, None),
+    ("dfloat", 1.0): (1e-6, 1e-4), ("dfloat", 2.0): (1e-6, 1e-4), ("dfloat", 3.0): (1e-6, 1e-4),
 }
 
 
