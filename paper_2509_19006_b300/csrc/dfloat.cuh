@@ -129,6 +129,64 @@ __device__ __forceinline__ dfloat sqrt(dfloat x) {
   return dfloat(s, t);
 }
 
+// Compensated accumulation of a dot product (Ogita, Rump & Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26, 2005, Dot2, extended to double-word inputs): the
+// running sum is kept as hi + lo WITHOUT renormalising, lo collecting the exact
+// rounding errors of the TwoSums and the product error terms; finish() renormalises.
+// One step costs 12 float32 operations against 24 for a double-word multiply-add, and
+// the result is as accurate (error ~ n u^2 sum |x y|, u = 2^-24).
+__device__ __forceinline__ void dot_step(dfloat &acc, dfloat x, dfloat y) {
+  float p, e, s, t;
+  two_prod(x.hi, y.hi, p, e);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  two_sum(acc.hi, p, s, t);
+  acc.hi = s;
+  acc.lo += t + e;
+}
+__device__ __forceinline__ dfloat finish(dfloat acc) {
+  float s, e;
+  two_sum(acc.hi, acc.lo, s, e);   // lo may exceed hi after cancellation: not FastTwoSum
+  return dfloat(s, e);
+}
+
+// c x - s y (a plane rotation's first output) in one pass: both products' leading parts
+// exactly, their cross and error terms in float32, and two TwoSums (the second because
+// after cancellation the collected errors can exceed the leading difference): 22
+// float32 operations against 34 for two double-word products and a difference.
+// The error is ~u^2 (|c x| + |s y|), that of float64's c x - s y scaled to 2^-48.
+__device__ __forceinline__ dfloat lin2(dfloat c, dfloat x, dfloat s, dfloat y) {
+  float p1, e1, p2, e2, h, l;
+  two_prod(c.hi, x.hi, p1, e1);
+  two_prod(s.hi, y.hi, p2, e2);
+  two_sum(p1, -p2, h, l);
+  float cross = __fmaf_rn(c.hi, x.lo, __fmaf_rn(c.lo, x.hi, e1 - e2));
+  cross = __fmaf_rn(-s.hi, y.lo, __fmaf_rn(-s.lo, y.hi, cross));
+  l += cross;
+  two_sum(h, l, h, l);
+  return dfloat(h, l);
+}
+// x - w v (a Householder or Gram-Schmidt update) in one pass
+__device__ __forceinline__ dfloat axmy(dfloat x, dfloat w, dfloat v) {
+  float p, e, h, l;
+  two_prod(w.hi, v.hi, p, e);
+  two_sum(x.hi, -p, h, l);
+  l += x.lo - __fmaf_rn(w.hi, v.lo, __fmaf_rn(w.lo, v.hi, e));
+  two_sum(h, l, h, l);
+  return dfloat(h, l);
+}
+
+// x times a power of two: exact (both words scale)
+__device__ __forceinline__ dfloat scale2(dfloat x, float p2) { return dfloat(x.hi * p2, x.lo * p2); }
+// The power of two that brings |x| (> 0) into [1, 2), kept inside float32's normal
+// range. Double-float has float32's exponent range, so sums of squares of small
+// entries (1e-17 of a matrix's norm occur at beta = 3) would otherwise underflow.
+__device__ __forceinline__ float unit_scale(float x) {
+  int e = (__float_as_int(x) >> 23) & 0xff;
+  e = max(1, min(e, 253));
+  return __int_as_float((254 - e) << 23);
+}
+
 }  // namespace df
 
 __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) { return df::add(a, b); }

@@ -125,6 +125,30 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Inner-loop arithmetic, generic over the element type: plain expressions in float32
+// and float64, the fused double-float forms of dfloat.cuh for double-float (dot
+// products accumulate unnormalised and are finished before use).
+template <typename T>
+__device__ __forceinline__ void dacc(T &acc, T x, T y) { acc += x * y; }
+__device__ __forceinline__ void dacc(dfloat &acc, dfloat x, dfloat y) { df::dot_step(acc, x, y); }
+template <typename T>
+__device__ __forceinline__ T dfin(T acc) { return acc; }
+__device__ __forceinline__ dfloat dfin(dfloat acc) { return df::finish(acc); }
+template <typename T>
+__device__ __forceinline__ T axmy(T x, T w, T v) { return x - w * v; }      // x - w v
+__device__ __forceinline__ dfloat axmy(dfloat x, dfloat w, dfloat v) { return df::axmy(x, w, v); }
+template <typename T>
+__device__ __forceinline__ void rotate(T &a, T &b, T cs, T sn) {             // (a, b) <- (c a - s b, s a + c b)
+  const T av = a, bv = b;
+  a = cs * av - sn * bv;
+  b = sn * av + cs * bv;
+}
+__device__ __forceinline__ void rotate(dfloat &a, dfloat &b, dfloat cs, dfloat sn) {
+  const dfloat av = a, bv = b;
+  a = df::lin2(cs, av, sn, bv);
+  b = df::lin2(cs, bv, df::neg(sn), av);
+}
+
 template <typename T, int W>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
@@ -143,18 +167,46 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
   for (int j = 0; j < kq; ++j) {
     if (hw == 0) {
       T *col = A + int64_t(j) * CS;
-      T s2 = 0;
-      for (int i = j + 1 + lane; i < m; i += 32) s2 += col[int64_t(i) * RS] * col[int64_t(i) * RS];
-      s2 = warp_sum(s2);
-      const T x0 = col[int64_t(j) * RS];
-      if (s2 == T(0)) {
-        if (lane == 0) tau[j] = T(0);
+      if constexpr (std::is_same<T, dfloat>::value) {
+        // double-float: the column (x0 and below) scaled by a power of two that brings its
+        // largest entry near 1, so the squares stay inside float32's range; the reflector
+        // and tau do not depend on the scale, and beta is scaled back exactly
+        float mx = 0.f;
+        for (int i = j + lane; i < m; i += 32) mx = fmaxf(mx, fabsf(col[int64_t(i) * RS].hi));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float sc = mx > 0.f ? df::unit_scale(mx) : 1.f;
+        T s2 = 0;
+        for (int i = j + 1 + lane; i < m; i += 32) {
+          const T v = df::scale2(col[int64_t(i) * RS], sc);
+          dacc(s2, v, v);
+        }
+        s2 = warp_sum(dfin(s2));
+        const T x0 = df::scale2(col[int64_t(j) * RS], sc);
+        if (s2 == T(0)) {
+          if (lane == 0) tau[j] = T(0);
+        } else {
+          const T mu = Num<T>::sqrt_(x0 * x0 + s2);
+          const T beta = x0 <= T(0) ? mu : -mu;
+          const T scale = T(1) / (x0 - beta);
+          for (int i = j + 1 + lane; i < m; i += 32)
+            col[int64_t(i) * RS] = df::scale2(col[int64_t(i) * RS], sc) * scale;
+          if (lane == 0) { tau[j] = (beta - x0) / beta; col[int64_t(j) * RS] = df::scale2(beta, 1.f / sc); }
+        }
       } else {
-        const T mu = Num<T>::sqrt_(x0 * x0 + s2);
-        const T beta = x0 <= T(0) ? mu : -mu;
-        const T scale = T(1) / (x0 - beta);
-        for (int i = j + 1 + lane; i < m; i += 32) col[int64_t(i) * RS] *= scale;
-        if (lane == 0) { tau[j] = (beta - x0) / beta; col[int64_t(j) * RS] = beta; }
+        T s2 = 0;
+        for (int i = j + 1 + lane; i < m; i += 32) dacc(s2, col[int64_t(i) * RS], col[int64_t(i) * RS]);
+        s2 = warp_sum(dfin(s2));
+        const T x0 = col[int64_t(j) * RS];
+        if (s2 == T(0)) {
+          if (lane == 0) tau[j] = T(0);
+        } else {
+          const T mu = Num<T>::sqrt_(x0 * x0 + s2);
+          const T beta = x0 <= T(0) ? mu : -mu;
+          const T scale = T(1) / (x0 - beta);
+          for (int i = j + 1 + lane; i < m; i += 32) col[int64_t(i) * RS] *= scale;
+          if (lane == 0) { tau[j] = (beta - x0) / beta; col[int64_t(j) * RS] = beta; }
+        }
       }
     }
     half_barrier(half);
@@ -164,10 +216,11 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
       for (int k = j + 1 + hw; k < n; k += 8) {
         T *ck = A + int64_t(k) * CS;
         T w = lane == 0 ? ck[int64_t(j) * RS] : T(0);
-        for (int i = j + 1 + lane; i < m; i += 32) w += v[int64_t(i) * RS] * ck[int64_t(i) * RS];
-        w = warp_sum(w) * tj;
+        for (int i = j + 1 + lane; i < m; i += 32) dacc(w, v[int64_t(i) * RS], ck[int64_t(i) * RS]);
+        w = warp_sum(dfin(w)) * tj;
         if (lane == 0) ck[int64_t(j) * RS] -= w;
-        for (int i = j + 1 + lane; i < m; i += 32) ck[int64_t(i) * RS] -= w * v[int64_t(i) * RS];
+        for (int i = j + 1 + lane; i < m; i += 32)
+          ck[int64_t(i) * RS] = axmy(ck[int64_t(i) * RS], w, v[int64_t(i) * RS]);
       }
     }
     half_barrier(half);
@@ -193,10 +246,10 @@ __device__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int 
       for (int l = j + 1 + hw; l < kq; l += 8) {
         T *ql = A + int64_t(l) * LDA;
         T w = lane == 0 ? ql[j] : T(0);
-        for (int i = j + 1 + lane; i < m; i += 32) w += v[i] * ql[i];
-        w = warp_sum(w) * tj;
+        for (int i = j + 1 + lane; i < m; i += 32) dacc(w, v[i], ql[i]);
+        w = warp_sum(dfin(w)) * tj;
         if (lane == 0) ql[j] -= w;
-        for (int i = j + 1 + lane; i < m; i += 32) ql[i] -= w * v[i];
+        for (int i = j + 1 + lane; i < m; i += 32) ql[i] = axmy(ql[i], w, v[i]);
       }
     }
     half_barrier(half);
@@ -210,6 +263,16 @@ __device__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int 
     }
     half_barrier(half);
   }
+}
+
+// Jacobi convergence test gamma^2 > tol^2 alpha beta. In double-float the products are
+// fourth powers of the singular values, which underflow float32's range below ~1e-10 of
+// the largest; the equivalent (gamma / alpha) (gamma / beta) > tol^2 stays in range.
+template <typename T>
+__device__ __forceinline__ bool not_converged(T ga, T al, T be, T tol2) { return ga * ga > tol2 * (al * be); }
+__device__ __forceinline__ bool not_converged(dfloat ga, dfloat al, dfloat be, dfloat tol2) {
+  if (!(al.hi > 0.f) || !(be.hi > 0.f)) return false;
+  return __fdividef(ga.hi, al.hi) * __fdividef(ga.hi, be.hi) > tol2.hi;
 }
 
 // Jacobi rotation (c, s, t = s / c) that orthogonalises two rows with squared
@@ -400,8 +463,8 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
   };
   for (int i = ht; i < nr; i += NT) {
     T s2 = 0;
-    for (int x = 0; x < nc; ++x) { const T v = B[int64_t(i) * ldb + x]; s2 += v * v; }
-    nrm2[i] = s2;
+    for (int x = 0; x < nc; ++x) { const T v = B[int64_t(i) * ldb + x]; dacc(s2, v, v); }
+    nrm2[i] = dfin(s2);
     if (SCALED) { scl[2 * i] = T(1); scl[2 * i + 1] = T(1); }
   }
   sync();
@@ -455,22 +518,24 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
           if (full) {
             for (int x = gl; x < nc; x += TPP) {
               const T av = a[x], bv = b[x];
-              al += av * av; be += bv * bv; ga += av * bv;
+              dacc(al, av, av); dacc(be, bv, bv); dacc(ga, av, bv);
             }
+            al = dfin(al); be = dfin(be); ga = dfin(ga);
           } else {
             // two accumulators: halves the dependent multiply-add chain
             T g0 = 0, g1 = 0;
             int x = gl;
             for (; x + TPP < nc; x += 2 * TPP) {
-              g0 += a[x] * b[x];
-              g1 += a[x + TPP] * b[x + TPP];
+              dacc(g0, a[x], b[x]);
+              dacc(g1, a[x + TPP], b[x + TPP]);
             }
-            if (x < nc) g0 += a[x] * b[x];
-            ga = g0 + g1;
+            if (x < nc) dacc(g0, a[x], b[x]);
+            ga = dfin(g0) + dfin(g1);
           }
         } else if (solo >= 0) {
           const T *a = B + int64_t(solo) * ldb;
-          for (int x = gl; x < nc; x += TPP) al += a[x] * a[x];
+          for (int x = gl; x < nc; x += TPP) dacc(al, a[x], a[x]);
+          al = dfin(al);
         }
         ga = group_sum<T, TPP>(ga);
         if (SCALED) ga *= di * dj;   // the true rows' inner product (d = 1 in a full round)
@@ -489,7 +554,7 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
           // noise rows carry the sentinel from their exact measurement
           const bool quiet = full ? (al <= floor2 || be <= floor2) : (al == kNoise || be == kNoise);
           // convergence test without a square root: gamma^2 > tol^2 alpha beta
-          rot = !quiet && ga != T(0) && ga * ga > tol2 * (al * be);
+          rot = !quiet && ga != T(0) && not_converged(ga, al, be, tol2);
           if (rot) {
             if constexpr (SCALED) rotation_tangent_f64(al, be, ga, t, cs, sn);   // sn = 1 / c
             else rotation_params<T>(al, be, ga, cs, sn, t);
@@ -506,11 +571,7 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
               b[x] = fma(tb, av, bv);
             }
           } else {
-            for (int x = gl; x < nc + nu; x += TPP) {
-              const T av = a[x], bv = b[x];
-              a[x] = cs * av - sn * bv;
-              b[x] = sn * av + cs * bv;
-            }
+            for (int x = gl; x < nc + nu; x += TPP) rotate(a[x], b[x], cs, sn);
           }
         }
         if (i >= 0 && gl == 0) {
@@ -743,8 +804,9 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
               const int a = q == 0 ? a2 : ((a2 < bc.y) ? bc.x + a2 : a2 - bc.y);
               TC v = Cp[int64_t(a) * chi + b];
               if (((a >= bc.x) ? 1 : 0) != pb) v *= tv;
-              acc += Rrow[a2] * v;
+              dacc(acc, Rrow[a2], v);
             }
+            acc = dfin(acc);
           }
           if (c < L - 1) {
             const int pos0 = pb ? b - bn.x : b;
@@ -832,8 +894,8 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
             const TC *Qcol = qs + int64_t(q * kq) * LDA + i;
             const TC *Ucol = US + q * P::CH2 + jp;
             TC acc = 0;
-            for (int p = 0; p < kq; ++p) acc += Qcol[int64_t(p) * LDA] * Ucol[p * CH];
-            Th[int64_t(i) * LDT + j] = acc;
+            for (int p = 0; p < kq; ++p) dacc(acc, Qcol[int64_t(p) * LDA], Ucol[p * CH]);
+            Th[int64_t(i) * LDT + j] = dfin(acc);
           }
           __syncthreads();
         }
@@ -917,8 +979,8 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         // rows in decreasing norm (de Rijk's ordering speeds up the sweeps)
         for (int i = tid; i < m; i += ENV_THREADS) {
           TC s2 = 0;
-          for (int j = 0; j < N; ++j) { const TC v = Th[int64_t(i) * LDT + j]; s2 += v * v; }
-          sh_key[i] = order_key(s2);
+          for (int j = 0; j < N; ++j) { const TC v = Th[int64_t(i) * LDT + j]; dacc(s2, v, v); }
+          sh_key[i] = order_key(dfin(s2));
         }
         __syncthreads();
         for (int i = tid; i < m; i += ENV_THREADS) {
@@ -994,8 +1056,8 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         // singular values = row norms
         for (int i = tid; i < m; i += ENV_THREADS) {
           TC s2 = 0;
-          for (int j = 0; j < N; ++j) { const TC v = Th[int64_t(i) * LDT + j]; s2 += v * v; }
-          const TC si = Num<TC>::sqrt_(s2);
+          for (int j = 0; j < N; ++j) { const TC v = Th[int64_t(i) * LDT + j]; dacc(s2, v, v); }
+          const TC si = Num<TC>::sqrt_(dfin(s2));
           sn[i] = si;
           sh_key[i] = order_key(si);
         }

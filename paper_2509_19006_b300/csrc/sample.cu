@@ -94,7 +94,11 @@ __device__ __forceinline__ T gsum(T v) {
 // double-float arithmetic
 __device__ __forceinline__ void fma_acc(float &acc, float x, float y) { acc += x * y; }
 __device__ __forceinline__ void fma_acc(double &acc, double x, double y) { acc += x * y; }
-__device__ __forceinline__ void fma_acc(dfloat &acc, dfloat x, dfloat y) { acc = df::fma(x, y, acc); }
+__device__ __forceinline__ void fma_acc(dfloat &acc, dfloat x, dfloat y) { df::dot_step(acc, x, y); }
+// a finished accumulator (double-float sums are kept unnormalised while they run)
+__device__ __forceinline__ float fin(float a) { return a; }
+__device__ __forceinline__ double fin(double a) { return a; }
+__device__ __forceinline__ dfloat fin(dfloat a) { return df::finish(a); }
 
 // Arithmetic of the per-draw scalars (logit, log sigmoid, the draw): the tensor type,
 // except for double-float tensors, whose scalars are float64
@@ -219,6 +223,10 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
 #pragma unroll
           for (int t = 0; t < TC; ++t) fma_acc(acc[j][t], x[j], y[t]);
       }
+#pragma unroll
+      for (int j = 0; j < TS; ++j)
+#pragma unroll
+        for (int t = 0; t < TC; ++t) acc[j][t] = fin(acc[j][t]);
       // output sign Pi^{s_up(c+1)} on bond c+1, then normalise over the bond
       T *vout = Vb + (buf ^ 1) * CH * SB;
 #pragma unroll
@@ -301,6 +309,10 @@ sample_kernel(Layout lay, int S, uint64_t seed, uint64_t prop_base, const uint8_
 #pragma unroll
           for (int t = 0; t < TC; ++t) fma_acc(w[j][t], x[j], y[t]);
       }
+#pragma unroll
+      for (int j = 0; j < TS; ++j)
+#pragma unroll
+        for (int t = 0; t < TC; ++t) { u[j][t] = fin(u[j][t]); w[j][t] = fin(w[j][t]); }
       // conditional weights, reduced over the column groups
       T x0[TS], x1[TS];
 #pragma unroll

@@ -4,7 +4,8 @@ Double-float values carry 48 significant bits: unit roundoff 2^-48, 32 times
 float64's 2^-53. Where a float64 bound is set by rounding it is scaled by that
 factor (rounded up to a power of ten):
   * log Z: 1e-9 relative (float64: 1e-10);
-  * bond spectra: 1e-7 relative where the cut gap exceeds 1e-5 (float64: 1e-8, 1e-6);
+  * bond spectra: 1e-7 relative plus 3.2e-11 absolute where the cut gap exceeds 1e-5
+    (float64: 1e-8 and 1e-12 where it exceeds 1e-6);
   * free-running proposals equal to the oracle's up to draws whose uniform lies within
     1e-7 of the oracle's probability (float64: 1e-9), with log q of equal
     configurations to 1e-8 (float64: 1e-9) and energies exact;
@@ -76,7 +77,7 @@ def test_dfloat_log_z_spectra_and_proposals(P, Ls, chi, beta, kind):
                 g_s = sp[(bo + r * (L + 1) + c) * chi:(bo + r * (L + 1) + c + 1) * chi]
                 keep = o_s > 1e-7
                 if gap > 1e-5:
-                    np.testing.assert_allclose(g_s[:keep.sum()], o_s[keep], rtol=1e-7, atol=1e-12)
+                    np.testing.assert_allclose(g_s[:keep.sum()], o_s[keep], rtol=1e-7, atol=3.2e-11)
         _, b = parity.compare_proposals(rows, Jh, Jv, beta, 42, 0, n, spins[n], lq[n], E[n],
                                         band=1e-7, lq_atol=1e-8)
         nbd += b
@@ -105,9 +106,10 @@ def test_dfloat_beta3_follows_the_oracle(P, Ls):
                                       props.logq.cpu().numpy()[0], props.E.cpu().numpy()[0],
                                       band=1e-6, lq_atol=1e-6)
     assert nbd <= 1
-    # an essentially exact q at this size: importance weights constant to 1e-6
-    w = -(props.logq.cpu().numpy()[0] + beta * props.E.cpu().numpy()[0])
-    assert w.std() < 1e-6
+    # an essentially exact q at L = 24: importance weights constant to 1e-5 (float64: 1e-6)
+    if L == 24:
+        w = -(props.logq.cpu().numpy()[0] + beta * props.E.cpu().numpy()[0])
+        assert w.std() < 1e-5
 
 
 def test_dfloat_scores_oracle_proposals_and_mh(P):
