@@ -213,14 +213,35 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
     const T tj = tau[j];
     if (tj != T(0)) {
       const T *v = A + int64_t(j) * CS;
-      for (int k = j + 1 + hw; k < n; k += 8) {
-        T *ck = A + int64_t(k) * CS;
-        T w = lane == 0 ? ck[int64_t(j) * RS] : T(0);
-        for (int i = j + 1 + lane; i < m; i += 32) dacc(w, v[int64_t(i) * RS], ck[int64_t(i) * RS]);
-        w = warp_sum(dfin(w)) * tj;
-        if (lane == 0) ck[int64_t(j) * RS] -= w;
-        for (int i = j + 1 + lane; i < m; i += 32)
-          ck[int64_t(i) * RS] = axmy(ck[int64_t(i) * RS], w, v[int64_t(i) * RS]);
+      if constexpr (std::is_same<T, dfloat>::value) {
+        // double-float: 8 lanes per column (32 columns at a time), 3-level reductions
+        // (the trip count is uniform over the half: every lane reaches the shuffles)
+        constexpr int G = 8;
+        const int grp = ht / G, gl = ht % G;
+        for (int k0 = j + 1; k0 < n; k0 += 256 / G) {
+          const int k = k0 + grp;
+          const bool on = k < n;
+          T *ck = A + int64_t(on ? k : j) * CS;
+          T w = (on && gl == 0) ? ck[int64_t(j) * RS] : T(0);
+          if (on)
+            for (int i = j + 1 + gl; i < m; i += G) dacc(w, v[int64_t(i) * RS], ck[int64_t(i) * RS]);
+          w = group_sum<T, G>(dfin(w)) * tj;
+          if (on) {
+            if (gl == 0) ck[int64_t(j) * RS] -= w;
+            for (int i = j + 1 + gl; i < m; i += G)
+              ck[int64_t(i) * RS] = axmy(ck[int64_t(i) * RS], w, v[int64_t(i) * RS]);
+          }
+        }
+      } else {
+        for (int k = j + 1 + hw; k < n; k += 8) {
+          T *ck = A + int64_t(k) * CS;
+          T w = lane == 0 ? ck[int64_t(j) * RS] : T(0);
+          for (int i = j + 1 + lane; i < m; i += 32) dacc(w, v[int64_t(i) * RS], ck[int64_t(i) * RS]);
+          w = warp_sum(dfin(w)) * tj;
+          if (lane == 0) ck[int64_t(j) * RS] -= w;
+          for (int i = j + 1 + lane; i < m; i += 32)
+            ck[int64_t(i) * RS] = axmy(ck[int64_t(i) * RS], w, v[int64_t(i) * RS]);
+        }
       }
     }
     half_barrier(half);
@@ -243,13 +264,32 @@ __device__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int 
     const T tj = tau[j];
     if (tj != T(0)) {
       const T *v = A + int64_t(j) * LDA;
-      for (int l = j + 1 + hw; l < kq; l += 8) {
-        T *ql = A + int64_t(l) * LDA;
-        T w = lane == 0 ? ql[j] : T(0);
-        for (int i = j + 1 + lane; i < m; i += 32) dacc(w, v[i], ql[i]);
-        w = warp_sum(dfin(w)) * tj;
-        if (lane == 0) ql[j] -= w;
-        for (int i = j + 1 + lane; i < m; i += 32) ql[i] = axmy(ql[i], w, v[i]);
+      if constexpr (std::is_same<T, dfloat>::value) {
+        // double-float: 8 lanes per column, as in the factorisation
+        constexpr int G = 8;
+        const int grp = ht / G, gl = ht % G;
+        for (int l0 = j + 1; l0 < kq; l0 += 256 / G) {   // uniform trip count over the half
+          const int l = l0 + grp;
+          const bool on = l < kq;
+          T *ql = A + int64_t(on ? l : j) * LDA;
+          T w = (on && gl == 0) ? ql[j] : T(0);
+          if (on)
+            for (int i = j + 1 + gl; i < m; i += G) dacc(w, v[i], ql[i]);
+          w = group_sum<T, G>(dfin(w)) * tj;
+          if (on) {
+            if (gl == 0) ql[j] -= w;
+            for (int i = j + 1 + gl; i < m; i += G) ql[i] = axmy(ql[i], w, v[i]);
+          }
+        }
+      } else {
+        for (int l = j + 1 + hw; l < kq; l += 8) {
+          T *ql = A + int64_t(l) * LDA;
+          T w = lane == 0 ? ql[j] : T(0);
+          for (int i = j + 1 + lane; i < m; i += 32) dacc(w, v[i], ql[i]);
+          w = warp_sum(dfin(w)) * tj;
+          if (lane == 0) ql[j] -= w;
+          for (int i = j + 1 + lane; i < m; i += 32) ql[i] = axmy(ql[i], w, v[i]);
+        }
       }
     }
     half_barrier(half);
@@ -681,10 +721,13 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         if (!sh_go) break;
         const int nu = sh_task[0], N = sh_task[1], row0 = sh_task[3], rows = sh_task[4];
         if (tid == 0) sh_lastrot[0] = -1;
-        const int nsw = tid < 256
-                            ? jacobi_rows<TC, 8>(Th, rows, N, nu, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src,
-                                                 sh_scl)
-                            : 0;
+        int nsw;
+        if constexpr (std::is_same<TC, dfloat>::value)   // double-float rounds: the whole CTA
+          nsw = jacobi_rows<TC, 16, 512>(Th, rows, N, nu, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src, sh_scl);
+        else
+          nsw = tid < 256 ? jacobi_rows<TC, 8>(Th, rows, N, nu, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src,
+                                              sh_scl)
+                          : 0;
         __syncthreads();
         // the rotated rows back into the owner's Theta, sector 1 at its row row0
         for (int e = tid; e < rows * (N + nu); e += ENV_THREADS) {
@@ -1019,10 +1062,13 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           }
           // 8 lanes per row pair on one half (measured: faster than 4 lanes, and than
           // 16 lanes over the whole CTA, whose barrier costs more than its warps gain)
-          const int nsw0 = half == 0
-                               ? jacobi_rows<TC, 8>(Th, r0, N, k0, LDT, 0, ht, &sh_lastrot[0], Bnrm, sh_src,
-                                                    sh_scl)
-                               : 0;
+          int nsw0;
+          if constexpr (std::is_same<TC, dfloat>::value)   // double-float rounds: the whole CTA
+            nsw0 = jacobi_rows<TC, 16, 512>(Th, r0, N, k0, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src, sh_scl);
+          else
+            nsw0 = half == 0 ? jacobi_rows<TC, 8>(Th, r0, N, k0, LDT, 0, ht, &sh_lastrot[0], Bnrm, sh_src,
+                                                  sh_scl)
+                             : 0;
           if (tid == 0) {
             if (nsw0 > 0) { sh_sweeps += nsw0; sh_svds += 1; }
             if (send) {

@@ -105,6 +105,8 @@ def config(name: str) -> Workload:
         return Workload("L128_chi64_beta3_n8_S256", [128] * 8, 3.0, 64, 256)
     if name == "L64x64":    # the L=256 workload's sampler launch shape (64 x 256 chains) at L=64
         return Workload("L64_chi64_beta3_n64_S256", [64] * 64, 3.0, 64, 256)
+    if name == "L64x2":     # two realizations at L=64 (same beta, chi): one build launch for captures
+        return Workload("L64_chi64_beta3_n2_S64", [64] * 2, 3.0, 64, 64)
     if name == "L40x1":
         return Workload("L40_chi64_beta3_n1_S64", [40], 3.0, 64, 64)
     if name == "gauss128x8":   # 8 realizations of the Gaussian workload (profiler captures)
