@@ -357,6 +357,32 @@ tnmc_status tnmc_set_wait_budget(tnmc_handle *h, int64_t cycles);
  * Errors: TNMC_ERR_ARG (negative id), TNMC_ERR_CUDA. */
 tnmc_status tnmc_set_realization_ids(tnmc_handle *h, const int64_t *h_ids);
 
+/* Kernel layout of the environment build (the paper has no counterpart; every layout
+ * computes the same method and differs from the others in summation order only):
+ *   bits 0-1, the Jacobi SVD of a parity sector where a realization runs on a pair of
+ *     CTAs (float64, double-float): 0 = the precision's default (float64: 8 lanes per
+ *     row pair on half the CTA; double-float: 16 lanes on the whole CTA), 1 = 8 lanes
+ *     on the whole CTA, 2 = 8 lanes on half the CTA (3 is invalid);
+ *   bit 2 (4): one CTA per realization even where pairs of CTAs fit;
+ *   bit 3 (8): in the one-CTA build, 8 lanes per row pair instead of 4.
+ * Applies to later tnmc_build_envs calls (and the segment rebuilds of checkpointed
+ * handles). Errors: TNMC_ERR_ARG. */
+tnmc_status tnmc_set_build_variant(tnmc_handle *h, int32_t variant);
+
+/* The handle's current build layout (-1 for a NULL handle). */
+int32_t tnmc_get_build_variant(const tnmc_handle *h);
+
+/* Autotuner of the build layout (the paper has no counterpart): ingests d_J (as
+ * tnmc_build_envs), then for each candidate layout of the handle's precision builds
+ * only the bottom `rows` rows of every realization, timed with CUDA events on the
+ * handle's stream, and keeps the fastest for later builds. h_variants / h_ms (host,
+ * optional, capacity *h_count on entry) receive the candidates and their times in ms;
+ * *h_count receives the number of candidates. Synchronises the stream. The timing
+ * launches overwrite bottom rows of the cache, so the handle must be built again
+ * (tnmc_build_envs) before proposals. Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+tnmc_status tnmc_autotune_build(tnmc_handle *h, const float *d_J, int32_t rows, int32_t *h_variants,
+                                float *h_ms, int32_t *h_count);
+
 /* Copy the per-realization device flags (TNMC_FLAG_*) to h_flags [n_real],
  * after synchronising the stream; clears them when clear != 0.
  * Returns TNMC_OK, or TNMC_ERR_NUMERIC / TNMC_ERR_TIMEOUT if any flag of

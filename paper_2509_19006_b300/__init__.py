@@ -30,7 +30,8 @@ EXPORTED = [
     "tnmc_propose_static", "tnmc_propose_static_limit", "tnmc_set_correction",
     "tnmc_mlp_features", "tnmc_mlp_scratch_floats", "tnmc_mlp_grad", "tnmc_mlp_adam",
     "tnmc_mlp_pack", "tnmc_mlp_forward", "tnmc_mh_init_empty", "tnmc_set_wait_budget",
-    "tnmc_observables", "tnmc_set_realization_ids",
+    "tnmc_observables", "tnmc_set_realization_ids", "tnmc_set_build_variant",
+    "tnmc_get_build_variant", "tnmc_autotune_build",
 ]
 
 # learned proposal correction: parameter vector layout (include/tnmc.h)
@@ -85,6 +86,9 @@ def load_library():
         "tnmc_mh_init_empty": ([vp, vp, vp, vp], i32),
         "tnmc_set_wait_budget": ([vp, ctypes.c_int64], i32),
         "tnmc_set_realization_ids": ([vp, vp], i32),
+        "tnmc_set_build_variant": ([vp, i32], i32),
+        "tnmc_get_build_variant": ([vp], i32),
+        "tnmc_autotune_build": ([vp, vp, i32, vp, vp, vp], i32),
         "tnmc_observables": ([vp, i32, vp, vp, vp, vp], i32),
         "tnmc_mh_step": ([vp, i32, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "tnmc_set_diagnostics": ([vp, vp, vp, vp], i32),
@@ -391,6 +395,30 @@ class TNMC:
         assert arr.shape == (self.n_real,)
         _check(self.lib.tnmc_set_realization_ids(self.h, arr.ctypes.data_as(ctypes.c_void_p)),
                "tnmc_set_realization_ids")
+
+    def set_build_variant(self, variant: int):
+        """Kernel layout of the environment build (see include/tnmc.h)."""
+        _check(self.lib.tnmc_set_build_variant(self.h, int(variant)), "tnmc_set_build_variant")
+
+    @property
+    def build_variant(self) -> int:
+        return int(self.lib.tnmc_get_build_variant(self.h))
+
+    @_on_stream
+    def autotune(self, J, rows: int = 12):
+        """Time the candidate build layouts on the bottom `rows` rows of these realizations
+        and keep the fastest; returns {variant: ms}. Build again before proposing."""
+        import numpy as np
+        assert J.dtype == self.torch.float32 and J.is_cuda and J.is_contiguous()
+        cap = 16
+        var = np.zeros(cap, np.int32)
+        ms = np.zeros(cap, np.float32)
+        n = ctypes.c_int32(cap)
+        self._J_keep = J
+        _check(self.lib.tnmc_autotune_build(self.h, _ptr(J), int(rows), var.ctypes.data_as(ctypes.c_void_p),
+                                            ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)),
+               "tnmc_autotune_build")
+        return {int(v): float(t) for v, t in zip(var[:n.value], ms[:n.value])}
 
     def set_wait_budget(self, cycles: int):
         """Budget of the bounded device waits in SM cycles (0 = default, ~20 s)."""

@@ -256,6 +256,8 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
   lay.seg_begin = -1;
   lay.seg_end = 0;
   lay.wait_cycles = 0;
+  lay.variant = 0;
+  lay.tune_rows = 0;
   lay.ckpt64 = p.sum_ckpt > 0 ? reinterpret_cast<double *>(ws + p.off_ckpt64) : nullptr;
   lay.bonds = reinterpret_cast<int2 *>(ws + p.off_bonds);
   lay.lam = reinterpret_cast<double *>(ws + p.off_lam);
@@ -332,6 +334,54 @@ tnmc_status tnmc_set_realization_ids(tnmc_handle *h, const int64_t *h_ids) {
                                         h->stream);
   if (e == cudaSuccess) return cudaStreamSynchronize(h->stream) == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
   return TNMC_ERR_CUDA;
+}
+
+tnmc_status tnmc_set_build_variant(tnmc_handle *h, int32_t variant) {
+  if (!h || variant < 0 || variant > 15 || (variant & 3) == 3) return TNMC_ERR_ARG;
+  h->lay.variant = variant;
+  return TNMC_OK;
+}
+
+int32_t tnmc_get_build_variant(const tnmc_handle *h) { return h ? h->lay.variant : -1; }
+
+tnmc_status tnmc_autotune_build(tnmc_handle *h, const float *d_J, int32_t rows, int32_t *h_variants,
+                                float *h_ms, int32_t *h_count) {
+  if (!h || !d_J || rows < 1 || !h_count) return TNMC_ERR_ARG;
+  // candidate layouts of this precision (env_build.cu, VARIANT_*)
+  std::vector<int32_t> cand;
+  if (h->env_code == 0 || h->env_code == 3) cand = {0, 1, 2, 4, 4 | 8};
+  else cand = {0, 8};
+  cudaError_t e = launch_ingest(h->lay, d_J, h->stream);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+  int best = -1;
+  float best_ms = 0.f;
+  for (size_t k = 0; k < cand.size() && e == cudaSuccess; ++k) {
+    Layout l2 = h->lay;
+    l2.variant = cand[k];
+    l2.tune_rows = 1;                                         // loads the kernel: not timed
+    l2.dbg_logits = nullptr; l2.dbg_spectra = nullptr; l2.dbg_rowinfo = nullptr;
+    e = launch_env_build(l2, h->env_code, h->plan.CH, h->stream);
+    l2.tune_rows = rows;
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, h->stream);
+    if (e == cudaSuccess) e = launch_env_build(l2, h->env_code, h->plan.CH, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+    if (e != cudaSuccess) break;
+    if (h_variants && int(k) < *h_count) h_variants[k] = cand[k];
+    if (h_ms && int(k) < *h_count) h_ms[k] = ms;
+    if (best < 0 || ms < best_ms) { best = int(k); best_ms = ms; }
+  }
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  *h_count = int32_t(cand.size());
+  if (e != cudaSuccess) return TNMC_ERR_CUDA;
+  h->lay.variant = cand[best];
+  h->built = false;   // the timed launches overwrote bottom rows of the cache
+  return TNMC_OK;
 }
 
 tnmc_status tnmc_set_wait_budget(tnmc_handle *h, int64_t cycles) {

@@ -53,6 +53,8 @@ struct Layout {
   int32_t seg_begin;         // rows [seg_begin, seg_end) of this launch; seg_begin < 0 = all rows
   int32_t seg_end;
   int64_t wait_cycles;       // budget of a bounded device wait (0: the kernel's default)
+  int32_t variant;           // kernel layout of the environment build (env_build.cu, VARIANT_*)
+  int32_t tune_rows;         // > 0: build only each realization's bottom tune_rows rows (timing)
   double *ckpt64;            // MIXED with checkpoints: the checkpoint rows in float64, or null
   int2 *bonds;               // [sum L (L+1)]: (even, odd) dimension of bond b of row r
   double *lam;               // [sum L]: log scale lambda_r of row r

@@ -482,6 +482,7 @@ template <typename T, int TPP, int NT = 256, bool SCALED = false>
 __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int ht,
                            volatile int *lastrot, T *nrm2, const int *perm, T *scl) {
   static_assert(NT == 256 || NT == 512, "a half or the whole CTA");
+  static_assert(NT / TPP >= 32, "one lane group per row pair: up to 32 pairs (64 rows)");
   static_assert(!SCALED || std::is_same<T, double>::value, "scaled rotations are for float64 rows");
   if (nr <= 1) return 0;  // uniform over the half
   const int P = nr + (nr & 1);
@@ -647,6 +648,28 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
   return JACOBI_MAX_SWEEPS;
 }
 
+// Kernel layouts of the environment build, chosen at run time (Layout::variant):
+//   bits 0-1, Jacobi of a sector in a CTA pair (float64 and double-float):
+//     0 = the precision's default (float64: 8 lanes per row pair on half the CTA;
+//     double-float: 16 lanes on the whole CTA), 1 = 8 lanes on the whole CTA,
+//     2 = 8 lanes on half the CTA;
+//   bit 2, one CTA per realization even where CTA pairs fit;
+//   bit 3, Jacobi of the one-CTA build (both sectors, one per half): 0 = 4 lanes per
+//     row pair, 1 = 8 lanes.
+// Every layout computes the same method; they differ in summation order only.
+enum : int32_t { VARIANT_PAIR_MASK = 3, VARIANT_ONE_CTA = 4, VARIANT_SINGLE_8 = 8 };
+
+template <typename TC>
+__device__ __forceinline__ int jacobi_in_pair(int variant, TC *B, int nr, int nc, int nu, int ldb, int tid,
+                                              volatile int *lastrot, TC *nrm2, const int *perm, TC *scl) {
+  int code = variant & VARIANT_PAIR_MASK;
+  if (code == 0) code = std::is_same<TC, double>::value ? 2 : 0;
+  if (code == 1) return jacobi_rows<TC, 8, 512>(B, nr, nc, nu, ldb, 0, tid, lastrot, nrm2, perm, scl);
+  if (code == 2)
+    return tid < 256 ? jacobi_rows<TC, 8>(B, nr, nc, nu, ldb, 0, tid, lastrot, nrm2, perm, scl) : 0;
+  return jacobi_rows<TC, 16, 512>(B, nr, nc, nu, ldb, 0, tid, lastrot, nrm2, perm, scl);
+}
+
 // Non-negative floating-point values order like their bit patterns.
 __device__ __forceinline__ long long order_key(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ long long order_key(float x) { return (long long)__float_as_int(x); }
@@ -721,13 +744,8 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         if (!sh_go) break;
         const int nu = sh_task[0], N = sh_task[1], row0 = sh_task[3], rows = sh_task[4];
         if (tid == 0) sh_lastrot[0] = -1;
-        int nsw;
-        if constexpr (std::is_same<TC, dfloat>::value)   // double-float rounds: the whole CTA
-          nsw = jacobi_rows<TC, 16, 512>(Th, rows, N, nu, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src, sh_scl);
-        else
-          nsw = tid < 256 ? jacobi_rows<TC, 8>(Th, rows, N, nu, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src,
-                                              sh_scl)
-                          : 0;
+        const int nsw = jacobi_in_pair<TC>(lay.variant, Th, rows, N, nu, LDT, tid, &sh_lastrot[0], Bnrm,
+                                           sh_src, sh_scl);
         __syncthreads();
         // the rotated rows back into the owner's Theta, sector 1 at its row row0
         for (int e = tid; e < rows * (N + nu); e += ENV_THREADS) {
@@ -772,8 +790,9 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
     // rows of this launch: all (bottom-up), or one segment [a, b) rebuilt from
     // the checkpoint of row b (from the bottom row when b = L)
     const int K = lay.ckpt_every;
-    const int r_lo = lay.seg_begin < 0 ? 0 : lay.seg_begin;
+    int r_lo = lay.seg_begin < 0 ? 0 : lay.seg_begin;
     const int r_hi = lay.seg_begin < 0 ? L - 1 : min(lay.seg_end, L) - 1;
+    if (lay.tune_rows > 0) r_lo = max(0, L - lay.tune_rows);   // a timing launch: the bottom rows
     if (r_lo > r_hi) continue;   // uniform: this realization has no row in the segment
     int2 *bonds_n = lay.bonds + ri.bond_off;
     if (lay.flags[n] & FLAG_BAD_J) continue;  // uniform: read by all threads after the barrier
@@ -1062,13 +1081,8 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           }
           // 8 lanes per row pair on one half (measured: faster than 4 lanes, and than
           // 16 lanes over the whole CTA, whose barrier costs more than its warps gain)
-          int nsw0;
-          if constexpr (std::is_same<TC, dfloat>::value)   // double-float rounds: the whole CTA
-            nsw0 = jacobi_rows<TC, 16, 512>(Th, r0, N, k0, LDT, 0, tid, &sh_lastrot[0], Bnrm, sh_src, sh_scl);
-          else
-            nsw0 = half == 0 ? jacobi_rows<TC, 8>(Th, r0, N, k0, LDT, 0, ht, &sh_lastrot[0], Bnrm, sh_src,
-                                                  sh_scl)
-                             : 0;
+          const int nsw0 = jacobi_in_pair<TC>(lay.variant, Th, r0, N, k0, LDT, tid, &sh_lastrot[0], Bnrm,
+                                              sh_src, sh_scl);
           if (tid == 0) {
             if (nsw0 > 0) { sh_sweeps += nsw0; sh_svds += 1; }
             if (send) {
@@ -1090,10 +1104,13 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         } else {
           const int rows = half ? k1 : k0;
           TC *Bq = Th + int64_t(half ? k0 : 0) * LDT;
-          const int nsw = jacobi_rows<TC, 4, 256, std::is_same<TC, double>::value>(Bq, half ? r1 : r0, N, rows, LDT, half, ht,
-                                                                  &sh_lastrot[half],
-                                             Bnrm + (half ? CH : 0), sh_src + (half ? k0 : 0),
-                                             sh_scl + (half ? 2 * CH : 0));
+          const int rr = half ? r1 : r0;
+          TC *nb = Bnrm + (half ? CH : 0), *sc = sh_scl + (half ? 2 * CH : 0);
+          const int *pp = sh_src + (half ? k0 : 0);
+          const int nsw = (lay.variant & VARIANT_SINGLE_8)
+                              ? jacobi_rows<TC, 8, 256>(Bq, rr, N, rows, LDT, half, ht, &sh_lastrot[half], nb, pp, sc)
+                              : jacobi_rows<TC, 4, 256, std::is_same<TC, double>::value>(
+                                    Bq, rr, N, rows, LDT, half, ht, &sh_lastrot[half], nb, pp, sc);
           if (ht == 0 && nsw > 0) { atomicAdd(&sh_sweeps, nsw); atomicAdd(&sh_svds, 1); }
         }
         __syncthreads();
@@ -1320,8 +1337,9 @@ cudaError_t launch_env_build(const Layout &lay, int mode, int CH, cudaStream_t s
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (mode == 3) return launch_env_ts<dfloat, dfloat>(lay, CH, 2 * lay.env_slots <= sms, st);
-    return launch_env_ts<double, double>(lay, CH, 2 * lay.env_slots <= sms, st);
+    const bool pairs = 2 * lay.env_slots <= sms && !(lay.variant & VARIANT_ONE_CTA);
+    if (mode == 3) return launch_env_ts<dfloat, dfloat>(lay, CH, pairs, st);
+    return launch_env_ts<double, double>(lay, CH, pairs, st);
   }
   if (mode == 1) return launch_env_ts<float, float>(lay, CH, false, st);
   return launch_env_ts<double, float>(lay, CH, false, st);
