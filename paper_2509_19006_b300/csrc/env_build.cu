@@ -160,12 +160,62 @@ __device__ __forceinline__ T group_sum(T v) {
 // A[i * RS + j * CS]: R in the upper trapezoid, reflectors v (v_j = 1 implied)
 // below the diagonal, their coefficients in tau. (LAPACK's geqr2 scheme:
 // beta = -sign(x0)|x|.) RS = 1 is a column-major panel, CS = 1 a row-major one.
-template <typename T, int RS, int CS>
-__device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int ht) {
+//
+// With PIVOT (double-float preconditioning QR) the columns are pivoted (Businger & Golub,
+// 1965: at step j the remaining column of largest norm below row j is swapped into
+// place; LAPACK's geqp3 order): piv[k] receives the original index of column k and cn
+// holds the norms below the current row, recomputed exactly in each update pass (no
+// downdating). The triangular factor is then graded, and one-sided Jacobi on its rows
+// needs about half the sweeps (Drmac & Veselic, "New fast and accurate Jacobi SVD
+// algorithm", SIAM J. Matrix Anal. Appl. 29, 2008).
+template <typename T, int RS, int CS, bool PIVOT = false>
+__device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int ht, T *cn = nullptr,
+                                       int *piv = nullptr) {
   const int hw = ht >> 5, lane = ht & 31;
   const int kq = min(m, n);
+  if constexpr (PIVOT) {
+    static_assert(std::is_same<T, dfloat>::value, "pivoted QR is the double-float preconditioner");
+    constexpr int G = 8;
+    const int grp = ht / G, gl = ht % G;
+    for (int k0 = 0; k0 < n; k0 += 256 / G) {           // uniform trip count over the half
+      const int k = k0 + grp;
+      T s2 = 0;
+      if (k < n)
+        for (int i = gl; i < m; i += G) dacc(s2, A[int64_t(i) * RS + int64_t(k) * CS], A[int64_t(i) * RS + int64_t(k) * CS]);
+      s2 = group_sum<T, G>(dfin(s2));
+      if (k < n && gl == 0) { cn[k] = s2; piv[k] = k; }
+    }
+    half_barrier(half);
+  }
   for (int j = 0; j < kq; ++j) {
     if (hw == 0) {
+      if constexpr (PIVOT) {
+        // the remaining column of largest norm (ties: lower index) swapped into column j
+        float best = -1.f;
+        int bk = j;
+        for (int k = j + lane; k < n; k += 32) {
+          const float v = cn[k].hi;
+          if (v > best) { best = v; bk = k; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+          if (ov > best || (ov == best && ok < bk)) { best = ov; bk = ok; }
+        }
+        if (bk != j) {
+          for (int i = lane; i < m; i += 32) {
+            const T x = A[int64_t(i) * RS + int64_t(j) * CS];
+            A[int64_t(i) * RS + int64_t(j) * CS] = A[int64_t(i) * RS + int64_t(bk) * CS];
+            A[int64_t(i) * RS + int64_t(bk) * CS] = x;
+          }
+          if (lane == 0) {
+            const T c = cn[j]; cn[j] = cn[bk]; cn[bk] = c;
+            const int p = piv[j]; piv[j] = piv[bk]; piv[bk] = p;
+          }
+        }
+        __syncwarp();
+      }
       T *col = A + int64_t(j) * CS;
       if constexpr (std::is_same<T, dfloat>::value) {
         // double-float: the column (x0 and below) scaled by a power of two that brings its
@@ -211,7 +261,7 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
     }
     half_barrier(half);
     const T tj = tau[j];
-    if (tj != T(0)) {
+    if (tj != T(0) || PIVOT) {   // pivoting refreshes the column norms even for a null reflector
       const T *v = A + int64_t(j) * CS;
       if constexpr (std::is_same<T, dfloat>::value) {
         // double-float: 8 lanes per column (32 columns at a time), 3-level reductions
@@ -226,10 +276,18 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
           if (on)
             for (int i = j + 1 + gl; i < m; i += G) dacc(w, v[int64_t(i) * RS], ck[int64_t(i) * RS]);
           w = group_sum<T, G>(dfin(w)) * tj;
+          T nn = 0;
           if (on) {
             if (gl == 0) ck[int64_t(j) * RS] -= w;
-            for (int i = j + 1 + gl; i < m; i += G)
-              ck[int64_t(i) * RS] = axmy(ck[int64_t(i) * RS], w, v[int64_t(i) * RS]);
+            for (int i = j + 1 + gl; i < m; i += G) {
+              const T x = axmy(ck[int64_t(i) * RS], w, v[int64_t(i) * RS]);
+              ck[int64_t(i) * RS] = x;
+              if constexpr (PIVOT) dacc(nn, x, x);
+            }
+          }
+          if constexpr (PIVOT) {
+            nn = group_sum<T, G>(dfin(nn));
+            if (on && gl == 0) cn[k] = nn;
           }
         }
       } else {
@@ -692,6 +750,11 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   __shared__ int sh_lastrot[2];
   __shared__ int sh_keep[2 * CH];   // per candidate row: (sector << 16 | position) or -1
   __shared__ int sh_src[2 * CH];    // Jacobi row order, then kept bond index -> candidate row
+  // double-float preconditioning QR with column pivoting: per sector, the column norms and
+  // the permutation (piv: position -> original column; ipiv: original column -> position)
+  constexpr bool PIVQR = std::is_same<TC, dfloat>::value;
+  __shared__ TC sh_cn[PIVQR ? 2 * CH : 1];
+  __shared__ int sh_piv[PIVQR ? 2 * CH : 1], sh_ipiv[PIVQR ? 2 * CH : 1];
   __shared__ long long sh_key[2 * CH];   // ordering keys of the singular values
   __shared__ TC Bnrm[2 * CH];        // squared row norms cached by the Jacobi sweeps
   __shared__ TC sh_scl[4 * CH];      // Jacobi row scales (d, 1/d) of float64 rows, per sector
@@ -1015,7 +1078,13 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           TC *As = Th + int64_t(half ? k0 : 0) * LDT;
           TC *ts = tau + half * CH;
           TC *Qb = US + half * P::CH2;   // free until this site's U S is written
-          householder_qr_strided<TC, LDT, 1>(As, ks, N, ts, half, ht);
+          if constexpr (PIVQR) {
+            householder_qr_strided<TC, LDT, 1, true>(As, ks, N, ts, half, ht, sh_cn + half * CH,
+                                                     sh_piv + half * CH);
+            for (int b = ht; b < N; b += 256) sh_ipiv[half * CH + sh_piv[half * CH + b]] = b;
+          } else {
+            householder_qr_strided<TC, LDT, 1>(As, ks, N, ts, half, ht);
+          }
           // the reflectors to Q's column-major buffer, R's lower part cleared
           for (int e = ht; e < ks * rs; e += 256) {
             const int i = e / rs, j = e % rs;
@@ -1224,7 +1293,12 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         for (int e = tid; e < chi2; e += ENV_THREADS) {
           const int a = e / chi, b = e % chi;
           TC v = TC(0);
-          if (a < nk && b < N) { const int i = sh_src[a]; v = Th[int64_t(i) * LDT + b] * Bnrm[i]; }
+          if (a < nk && b < N) {
+            const int i = sh_src[a];
+            // pivoted preconditioning: column b of the site sits at position ipiv[b] of the rows
+            const int bb = PIVQR ? sh_ipiv[(i >= k0 ? CH : 0) + b] : b;
+            v = Th[int64_t(i) * LDT + bb] * Bnrm[i];
+          }
           dst[e] = TS(v);
           if (P::split_carry) cdst[e] = v;
         }
