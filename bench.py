@@ -146,20 +146,31 @@ def dist_env():
 
 
 # ----------------------------------------------------------------------- oracle arm
+# Mean bond dimension over all rows of the oracle's own full build of realization 0 of
+# the L = 256 workload (468 s on 8 threads): the bottom rows that a bounded sample can
+# time have smaller bonds, so their per-row cost is scaled by (D_all / D_timed)^3 (the
+# SVD cost). On that full build the model gives 345 s against the measured 468 s: the
+# extrapolated oracle is still credited with 1.36x its real speed.
+ORACLE_MEAN_BOND = {"L256_chi64_beta3_n64_S256": 43.31}
+
+
 def oracle_sample(wl, seconds: float = 15.0):
     """Time the FP64 oracle on a bounded sample of the workload.
 
     Realization 0: the environment rows are built from the bottom up until
     `seconds` have elapsed; the per-row cost of the last half of those rows is
-    extrapolated to all L rows. Proposals are not timed: the environment build
-    dominates the oracle's time, so this is an upper bound on its throughput.
+    extrapolated to all L rows, scaled by (D_all / D_timed)^3 where the workload's
+    all-row mean bond dimension D_all is known (ORACLE_MEAN_BOND). Proposals are not
+    timed: the environment build dominates the oracle's time, so this is an upper
+    bound on its throughput. Returns (seconds per realization, rows timed, wall s,
+    mean bond of the timed rows).
     """
     from oracle import bmps
     L, chi, beta = wl.Ls[0], wl.chi, wl.beta
     Jh, Jv = wl.realization(0)
     t0 = time.perf_counter()
     mps, lam = bmps.bottom_row_mps(Jh[L - 1], beta)
-    times = []
+    times, dims = [], []
     for r in range(L - 1, -1, -1):
         ts = time.perf_counter()
         if r < L - 1:
@@ -167,11 +178,26 @@ def oracle_sample(wl, seconds: float = 15.0):
             mps = bmps.multiply(mpo, mps)
         mps = bmps.compress(mps, chi)[0]
         times.append(time.perf_counter() - ts)
+        dims.append(float(np.mean([A.shape[2] for A in mps[:-1]])) if L > 1 else 1.0)
         if time.perf_counter() - t0 > seconds and len(times) >= 4:
             break
-    steady = times[len(times) // 2:]
-    per_row = sum(steady) / len(steady)
-    return per_row * L, len(times), time.perf_counter() - t0
+    half = len(times) // 2
+    per_row = sum(times[half:]) / len(times[half:])
+    d_timed = float(np.mean(dims[half:]))
+    d_all = ORACLE_MEAN_BOND.get(wl.name)
+    if d_all:
+        per_row *= (d_all / d_timed) ** 3
+    return per_row * L, len(times), time.perf_counter() - t0, d_timed
+
+
+def oracle_sample_text(wl, rows_done, d_timed, acceptance):
+    d_all = ORACLE_MEAN_BOND.get(wl.name)
+    scale = (f", scaled by (D_all / D_timed)^3 = ({d_all} / {d_timed:.1f})^3 for the larger bonds of "
+             f"the rows above (D_all: the oracle's own full build)" if d_all else "")
+    return (f"realization 0 of {wl.name}: bottom {rows_done} environment rows timed, per-row cost "
+            f"extrapolated to all {wl.Ls[0]} rows{scale}; proposals not timed; acceptance {acceptance} "
+            f"(the float64 method's at this workload, measured on the GPU: the oracle cannot run its "
+            f"own MH at this size)")
 
 
 def cpu_cores():
@@ -191,14 +217,11 @@ def run_reference(args, wl):
     for _ in range(args.warmup):
         oracle_sample(wl, seconds=args.ref_seconds / 3)
     for _ in range(args.steps):
-        t_real, rows_done, wall = oracle_sample(wl, seconds=args.ref_seconds)
+        t_real, rows_done, wall, d_timed = oracle_sample(wl, seconds=args.ref_seconds)
         # the oracle computes the same method; its acceptance is the method's (given)
         vals.append(wl.S * args.ref_acceptance / t_real)
     v = float(np.mean(vals))
-    sample = (f"realization 0 of {wl.name}: bottom {rows_done} environment rows timed, "
-              f"per-row cost extrapolated to all {wl.Ls[0]} rows; proposals not timed; "
-              f"acceptance {args.ref_acceptance} (that of the float64 method at this workload, "
-              f"measured on the GPU; the oracle cannot run its own MH at this size)")
+    sample = oracle_sample_text(wl, rows_done, d_timed, args.ref_acceptance)
     line = {"impl": "reference", "metric": metric_name(wl), "value": v, "unit": "accepted/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -265,6 +288,66 @@ def train_correction(P, t, J, wl, args, dev):
             "acceptance_teacher": a_teacher}
 
 
+def run_arm(P, gw, ids, args, prec, steps, dev):
+    """One precision timed on the same realizations (the headline comparison of the metric:
+    plain float64 against the mixed-precision form): `steps` full steps (ingest,
+    environments, log Z, S proposals, MH), each bracketed by CUDA events on the handle's
+    stream after an L2 flush. Chains start at the first proposal of the first step; the
+    acceptance counts only the MH decisions after that forced first acceptance."""
+    import torch
+    S = gw.S
+    my_Ls = [gw.Ls[g] for g in ids]
+    n = len(ids)
+    J = torch.from_numpy(gw.packed_J(ids)).to(dev)
+    t = P.TNMC(my_Ls, gw.chi, gw.beta, prec, max_samples=S, device=dev)
+    t.set_realization_ids(ids)
+    tune = t.autotune(J, rows=args.tune_rows) if args.tune_rows > 0 else {}
+    props = t.alloc_proposals(S)
+    acc = torch.empty((n, S), dtype=torch.uint8, device=dev)
+    logz = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    _, _, rowinfo = t.set_diagnostics(rowinfo=True)
+    state = t.mh_init_empty()
+    stream = t.stream
+    step_ms, env_ms, accepted, decided = [], [], 0, 0
+    for k in range(steps):
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            t.build_envs(J)
+            e1.record(stream)
+            t.log_z(out=logz)
+            t.propose(S, SAMPLING_SEED, 30_000_000 * (k + 1), out=props)
+            t.mh_step(props, state, SAMPLING_SEED, accept=acc)
+            e2.record(stream)
+        torch.cuda.synchronize()
+        a = int(acc.sum().item())
+        if k == 0:
+            a -= n                      # the forced first acceptance of every chain
+            decided += n * (S - 1)
+        else:
+            decided += n * S
+        accepted += a
+        step_ms.append(e0.elapsed_time(e2))
+        env_ms.append(e0.elapsed_time(e1))
+        if k == 0:
+            dmean = float(rowinfo.cpu().numpy().reshape(-1, 14)[:, 5].mean())
+            t.set_diagnostics()
+    st, _ = t.device_status()
+    step_s = sum(step_ms) / len(step_ms) / 1e3
+    acceptance = accepted / decided
+    out = {"precision": prec, "steps": steps, "step_s": step_s,
+           "env_build_s": sum(env_ms) / len(env_ms) / 1e3, "acceptance": acceptance,
+           "accepted_per_s": acceptance * n * S / step_s, "proposals_per_s": n * S / step_s,
+           "cutoff": t.cutoff, "bond_dim_mean": dmean, "device_status": int(st),
+           "build_variant": t.build_variant, "autotune_ms": tune}
+    del t, J, props, acc, logz, flush, state, rowinfo
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, wl):
     import torch
     import paper_2509_19006_b300 as P
@@ -293,6 +376,9 @@ def run_ours(args, wl):
                ckpt_every=ckpt)
     t.set_realization_ids(ids)
     n_mine = len(ids)
+    # the build layout: the autotuner times the candidates on the bottom rows of these
+    # realizations (setup, outside the timed region)
+    tune = t.autotune(J, rows=args.tune_rows) if args.tune_rows > 0 else {}
     stream = t.stream
     learned = None
     if args.learned:
@@ -409,6 +495,17 @@ def run_ours(args, wl):
         my_ms_all, accepted_all, e2e_s_all, e2e_acc_all = my_ms, accepted, e2e_s, e2e_acc
     assert int(full[:, 1].sum().item()) == int(accepted_all)
 
+    # ---------------- the headline comparison arms (one GPU; the primary handle is released
+    # first: the float64-sized caches of the arms do not fit beside it)
+    arms = []
+    cutoff_primary, plan_ch, variant_primary = t.cutoff, t.plan_ch, t.build_variant
+    if world == 1 and args.arms:
+        del t, props, state, acc, logz, flush
+        torch.cuda.empty_cache()
+        for spec in args.arms.split(","):
+            prec_a, steps_a = spec.split(":")
+            arms.append(run_arm(P, gw, ids, args, prec_a, int(steps_a), dev))
+
     if rank == 0:
         peaks = load_peaks()
         env_avg_s = sum(env_t) / len(env_t) / 1e3
@@ -429,7 +526,7 @@ def run_ours(args, wl):
         # realizations at L = 128 (131072 site-rows) read + wrote 2.203 GB; traffic grows
         # with the site-rows written
         site_rows = sum(L * L for L in my_Ls)
-        if args.prec == "fp32" and t.plan_ch == 64 and not ckpt:
+        if args.prec == "fp32" and plan_ch == 64 and not ckpt:
             traffic = 2.203e9 / 131072 * site_rows
             traffic_src = "ncu capture at L=128 x 8 realizations, scaled by site-rows"
         else:
@@ -443,13 +540,10 @@ def run_ours(args, wl):
         hbm_peak = peaks.get("hbm_gbs") or 6484.6
         cpu = None
         if world == 1 and args.cpu_baseline:
-            t_real, rows_done, _ = oracle_sample(wl, seconds=args.ref_seconds)
+            t_real, rows_done, _, d_timed = oracle_sample(wl, seconds=args.ref_seconds)
             cpu = {"value": S * args.ref_acceptance / t_real, "unit": "accepted/s", "cores": cpu_cores(),
                    "kind": "oracle",
-                   "sample": (f"FP64 oracle, realization 0 of {wl.name}: bottom {rows_done} environment "
-                              f"rows timed and extrapolated to {wl.Ls[0]} rows (proposals not timed); "
-                              f"credited with the float64 method's acceptance {args.ref_acceptance} "
-                              f"(the value the reference arm credits)")}
+                   "sample": "FP64 oracle, " + oracle_sample_text(wl, rows_done, d_timed, args.ref_acceptance)}
         line = {
             "metric": metric_name(wl),
             "value": accepted_all / (my_ms_all / 1e3),
@@ -463,7 +557,8 @@ def run_ours(args, wl):
                      else "synthetic +-J disorder (p = 1/2), seeded"),
             "config": {"workload": wl.name, "L": wl.Ls[0], "chi": wl.chi, "beta": wl.beta,
                        "realizations_per_gpu": wl.n_real, "realizations": n_all, "samples_per_realization": S,
-                       "precision": args.prec, "cutoff": t.cutoff, "ckpt_every": ckpt,
+                       "precision": args.prec, "cutoff": cutoff_primary, "ckpt_every": ckpt,
+                       "build_variant": variant_primary, "autotune_ms": tune,
                        "learned_correction": bool(args.learned),
                        "l2": "flushed (256 MB write) before every timed step; environment cache >> L2"},
             "acceptance": accepted / proposals,
@@ -500,6 +595,15 @@ def run_ours(args, wl):
         }
         if learned is not None:
             line["learned"] = learned
+        if arms:
+            by = {a["precision"]: a for a in arms}
+            line["headline"] = {
+                "what": ("the metric's comparison at this workload, measured in this run on the same "
+                         "realizations: plain float64 against the mixed-precision (double-float) form; "
+                         "accepted/s = acceptance x proposals / step time"),
+                "arms": arms,
+                "dfloat_over_fp64_accepted_per_s": (by["dfloat"]["accepted_per_s"] / by["fp64"]["accepted_per_s"]
+                                                    if "dfloat" in by and "fp64" in by else None)}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -704,6 +808,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--ref-acceptance", type=float, default=REF_ACCEPTANCE_L256)
+    ap.add_argument("--tune-rows", type=int, default=12,
+                    help="bottom rows the build autotuner times per layout (0: no autotuning)")
+    ap.add_argument("--arms", default=None,
+                    help="comparison arms 'prec:steps,...' timed after the primary line (default for "
+                         "the L256 workload: fp64:1,dfloat:2; '' for none)")
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="steps of the end-to-end leg (host buffers), at most --steps")
     ap.add_argument("--ckpt", type=int, default=-1,
@@ -724,6 +833,8 @@ def main():
                     help="build the environments once and exit (for profiler captures)")
     args = ap.parse_args()
     wl = config(args.workload)
+    if args.arms is None:
+        args.arms = "fp64:1,dfloat:2" if args.workload == "L256" and args.impl == "ours" else ""
     if args.sweep:
         run_sweep(args)
     elif args.serial_vs_batch:

@@ -306,48 +306,156 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
   }
 }
 
+// ---- double-float Householder QR and Q formation with one barrier per step.
+// Reflector of column j (entries j.. of col, stride RS) by one warp: the column scaled by
+// a power of two for the norm (float32's exponent range), as in householder_qr_strided.
+template <int RS>
+__device__ __forceinline__ void df_reflector(dfloat *col, int j, int m, dfloat *tau, int lane) {
+  float mx = 0.f;
+  for (int i = j + lane; i < m; i += 32) mx = fmaxf(mx, fabsf(col[int64_t(i) * RS].hi));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float sc = mx > 0.f ? df::unit_scale(mx) : 1.f;
+  dfloat s2 = 0;
+  for (int i = j + 1 + lane; i < m; i += 32) {
+    const dfloat v = df::scale2(col[int64_t(i) * RS], sc);
+    dacc(s2, v, v);
+  }
+  s2 = warp_sum(dfin(s2));
+  const dfloat x0 = df::scale2(col[int64_t(j) * RS], sc);
+  if (s2 == dfloat(0)) {
+    if (lane == 0) tau[j] = dfloat(0);
+  } else {
+    const dfloat mu = Num<dfloat>::sqrt_(x0 * x0 + s2);
+    const dfloat beta = x0 <= dfloat(0) ? mu : -mu;
+    const dfloat scale = dfloat(1) / (x0 - beta);
+    for (int i = j + 1 + lane; i < m; i += 32) col[int64_t(i) * RS] = df::scale2(col[int64_t(i) * RS], sc) * scale;
+    if (lane == 0) { tau[j] = (beta - x0) / beta; col[int64_t(j) * RS] = df::scale2(beta, 1.f / sc); }
+  }
+}
+
+// Householder QR (unpivoted) of the m x n panel A[i * RS + j * CS] by one half of the
+// CTA with look-ahead: in step j the first warp applies reflector j to column j + 1 and
+// at once computes reflector j + 1, while the other seven warps (8 lanes per column)
+// apply reflector j to columns j + 2 ..; one barrier per step. Same results as the
+// two-barrier form up to the order of the column-j+1 reductions.
+template <int RS, int CS>
+__device__ void householder_qr_la(dfloat *A, int m, int n, dfloat *tau, int half, int ht) {
+  const int hw = ht >> 5, lane = ht & 31;
+  const int kq = min(m, n);
+  if (kq <= 0) return;   // uniform over the half
+  if (hw == 0) df_reflector<RS>(A, 0, m, tau, lane);
+  half_barrier(half);
+  constexpr int G = 8;
+  const int grp = (ht - 32) / G, gl = (ht - 32) % G;   // warps 1..7: 28 lane groups
+  for (int j = 0; j < kq; ++j) {
+    const dfloat tj = tau[j];
+    const dfloat *v = A + int64_t(j) * CS;
+    if (hw == 0) {
+      if (j + 1 < n) {
+        dfloat *c1 = A + int64_t(j + 1) * CS;
+        if (tj != dfloat(0)) {
+          dfloat w = lane == 0 ? c1[int64_t(j) * RS] : dfloat(0);
+          for (int i = j + 1 + lane; i < m; i += 32) dacc(w, v[int64_t(i) * RS], c1[int64_t(i) * RS]);
+          w = warp_sum(dfin(w)) * tj;
+          if (lane == 0) c1[int64_t(j) * RS] -= w;
+          for (int i = j + 1 + lane; i < m; i += 32)
+            c1[int64_t(i) * RS] = axmy(c1[int64_t(i) * RS], w, v[int64_t(i) * RS]);
+        }
+        __syncwarp();
+        if (j + 1 < kq) df_reflector<RS>(c1, j + 1, m, tau, lane);
+      }
+    } else if (tj != dfloat(0)) {
+      for (int k0 = j + 2; k0 < n; k0 += 28) {   // uniform trip count over warps 1..7
+        const int k = k0 + grp;
+        const bool on = k < n;
+        dfloat *ck = A + int64_t(on ? k : j) * CS;
+        dfloat w = (on && gl == 0) ? ck[int64_t(j) * RS] : dfloat(0);
+        if (on)
+          for (int i = j + 1 + gl; i < m; i += G) dacc(w, v[int64_t(i) * RS], ck[int64_t(i) * RS]);
+        w = group_sum<dfloat, G>(dfin(w)) * tj;
+        if (on) {
+          if (gl == 0) ck[int64_t(j) * RS] -= w;
+          for (int i = j + 1 + gl; i < m; i += G)
+            ck[int64_t(i) * RS] = axmy(ck[int64_t(i) * RS], w, v[int64_t(i) * RS]);
+        }
+      }
+    }
+    half_barrier(half);
+  }
+}
+
+// Explicit Q from the reflectors (as form_q_inplace) with one barrier per step: column
+// j + 1 becomes H_{j+1} e_{j+1} at the start of step j, by the lane group that then
+// applies reflector j to it (the last step's update of it has passed the barrier).
+template <int LDA>
+__device__ void form_q_la(dfloat *A, const dfloat *tau, int m, int kq, int half, int ht) {
+  constexpr int G = 8;
+  const int grp = ht / G, gl = ht % G;
+  for (int j = kq - 1; j >= 0; --j) {
+    if (grp == 0 && j + 1 < kq) {
+      const dfloat t1 = tau[j + 1];
+      dfloat *q1 = A + int64_t(j + 1) * LDA;
+      for (int i = gl; i < m; i += G) {
+        if (i < j + 1) q1[i] = dfloat(0);
+        else if (i == j + 1) q1[i] = dfloat(1) - t1;
+        else q1[i] = -(t1 * q1[i]);
+      }
+    }
+    if (ht < 32) __syncwarp();   // the finalised column is read by other lanes of group 0
+    const dfloat tj = tau[j];
+    if (tj != dfloat(0)) {
+      const dfloat *v = A + int64_t(j) * LDA;
+      for (int l0 = j + 1; l0 < kq; l0 += 256 / G) {   // uniform trip count over the half
+        const int l = l0 + grp;
+        const bool on = l < kq;
+        dfloat *ql = A + int64_t(on ? l : j) * LDA;
+        dfloat w = (on && gl == 0) ? ql[j] : dfloat(0);
+        if (on)
+          for (int i = j + 1 + gl; i < m; i += G) dacc(w, v[i], ql[i]);
+        w = group_sum<dfloat, G>(dfin(w)) * tj;
+        if (on) {
+          if (gl == 0) ql[j] -= w;
+          for (int i = j + 1 + gl; i < m; i += G) ql[i] = axmy(ql[i], w, v[i]);
+        }
+      }
+    }
+    half_barrier(half);
+  }
+  if (kq > 0 && grp == 0) {   // column 0
+    const dfloat t0 = tau[0];
+    for (int i = gl; i < m; i += G) {
+      if (i == 0) A[0] = dfloat(1) - t0;
+      else A[i] = -(t0 * A[i]);
+    }
+  }
+  half_barrier(half);
+}
+
 // The column-major panel (ld LDA) of the left-to-right sweep.
 template <typename T, int LDA>
 __device__ __forceinline__ void householder_qr(T *A, int m, int n, T *tau, int half, int ht) {
-  householder_qr_strided<T, 1, LDA>(A, m, n, tau, half, ht);
+  if constexpr (std::is_same<T, dfloat>::value) householder_qr_la<1, LDA>(A, m, n, tau, half, ht);
+  else householder_qr_strided<T, 1, LDA>(A, m, n, tau, half, ht);
 }
 
 // Explicit Q (m x kq, column-major, ld LDA) formed in place of the reflectors
 // left in A (LAPACK's org2r order: last reflector first; column j becomes
 // H_j e_j once the columns to its right are final).
 template <typename T, int LDA>
-__device__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int ht) {
+__device__ void form_q_2b(T *A, const T *tau, int m, int kq, int half, int ht) {
   const int hw = ht >> 5, lane = ht & 31;
   for (int j = kq - 1; j >= 0; --j) {
     const T tj = tau[j];
     if (tj != T(0)) {
       const T *v = A + int64_t(j) * LDA;
-      if constexpr (std::is_same<T, dfloat>::value) {
-        // double-float: 8 lanes per column, as in the factorisation
-        constexpr int G = 8;
-        const int grp = ht / G, gl = ht % G;
-        for (int l0 = j + 1; l0 < kq; l0 += 256 / G) {   // uniform trip count over the half
-          const int l = l0 + grp;
-          const bool on = l < kq;
-          T *ql = A + int64_t(on ? l : j) * LDA;
-          T w = (on && gl == 0) ? ql[j] : T(0);
-          if (on)
-            for (int i = j + 1 + gl; i < m; i += G) dacc(w, v[i], ql[i]);
-          w = group_sum<T, G>(dfin(w)) * tj;
-          if (on) {
-            if (gl == 0) ql[j] -= w;
-            for (int i = j + 1 + gl; i < m; i += G) ql[i] = axmy(ql[i], w, v[i]);
-          }
-        }
-      } else {
-        for (int l = j + 1 + hw; l < kq; l += 8) {
-          T *ql = A + int64_t(l) * LDA;
-          T w = lane == 0 ? ql[j] : T(0);
-          for (int i = j + 1 + lane; i < m; i += 32) dacc(w, v[i], ql[i]);
-          w = warp_sum(dfin(w)) * tj;
-          if (lane == 0) ql[j] -= w;
-          for (int i = j + 1 + lane; i < m; i += 32) ql[i] = axmy(ql[i], w, v[i]);
-        }
+      for (int l = j + 1 + hw; l < kq; l += 8) {
+        T *ql = A + int64_t(l) * LDA;
+        T w = lane == 0 ? ql[j] : T(0);
+        for (int i = j + 1 + lane; i < m; i += 32) dacc(w, v[i], ql[i]);
+        w = warp_sum(dfin(w)) * tj;
+        if (lane == 0) ql[j] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) ql[i] = axmy(ql[i], w, v[i]);
       }
     }
     half_barrier(half);
@@ -361,6 +469,35 @@ __device__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int 
     }
     half_barrier(half);
   }
+}
+
+template <typename T, int LDA>
+__device__ __forceinline__ void form_q_inplace(T *A, const T *tau, int m, int kq, int half, int ht) {
+  if constexpr (std::is_same<T, dfloat>::value) form_q_la<LDA>(A, tau, m, kq, half, ht);
+  else form_q_2b<T, LDA>(A, tau, m, kq, half, ht);
+}
+
+// Sum over a lane group of W lanes for the Jacobi inner products. Double-float: a
+// compensated reduction (each level one TwoSum of the leading words, the exact error
+// and the trailing words summed in float32, renormalised at the end): absolute error
+// ~ u^2 (|x_1| + ... + |x_W|), enough for the convergence test (tolerance ~ 8 sqrt(n) u^2
+// relative to |a| |b|), at about half the latency of accurate double-word additions.
+template <typename T, int W>
+__device__ __forceinline__ T jgroup_sum(T v) { return group_sum<T, W>(v); }
+template <int W>
+__device__ __forceinline__ dfloat jgroup_sum_df(dfloat v) {
+  float h = v.hi, l = v.lo;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    df::two_sum(h, oh, s, e);
+    h = s;
+    l += ol + e;
+  }
+  float s, e;
+  df::two_sum(h, l, s, e);
+  return dfloat(s, e);
 }
 
 // Jacobi convergence test gamma^2 > tol^2 alpha beta. In double-float the products are
@@ -457,14 +594,20 @@ __device__ __forceinline__ void rotation_params<dfloat>(dfloat al, dfloat be, df
   }
   if (num == 0.f) tf = 1.f;
   const float c0 = rsqrtf(fmaf(tf, tf, 1.f));
-  float p, e;
-  df::two_prod(tf, tf, p, e);
-  const dfloat q = df::add(dfloat(1.f), dfloat(p, e));          // 1 + t^2
+  // d = c0^2 (1 + t^2) - 1 (|d| ~ 1e-7) from the exact products c0^2 = p + e and
+  // t^2 = tp + te: p (1 + tp) - 1 in one rounding (an FMA; p - 1 is exact), then the
+  // small terms e (1 + tp) + p te in float32: absolute error ~1e-15
+  float p, e, tp, te;
   df::two_prod(c0, c0, p, e);
-  const float d = df::add(df::mul(dfloat(p, e), q), dfloat(-1.f)).hi;
+  df::two_prod(tf, tf, tp, te);
+  const float d = fmaf(p, tp, p - 1.f) + fmaf(e, 1.f + tp, p * te);
   const float corr = d * fmaf(0.375f, d, -0.5f);
-  df::two_prod(c0, corr, p, e);
-  cs = df::add(dfloat(c0), dfloat(p, e));
+  // c = c0 + c0 corr with the product exact, s = c t
+  float ph, pl, ch, cl;
+  df::two_prod(c0, corr, ph, pl);
+  df::fast_two_sum(c0, ph, ch, cl);
+  cl += pl;
+  cs = dfloat(ch, cl);
   sn = df::mul(cs, tf);
   t = dfloat(tf);
 }
@@ -636,11 +779,17 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
           for (int x = gl; x < nc; x += TPP) dacc(al, a[x], a[x]);
           al = dfin(al);
         }
-        ga = group_sum<T, TPP>(ga);
+        if constexpr (std::is_same<T, dfloat>::value) ga = jgroup_sum_df<TPP>(ga);
+        else ga = group_sum<T, TPP>(ga);
         if (SCALED) ga *= di * dj;   // the true rows' inner product (d = 1 in a full round)
         if (full) {
-          al = group_sum<T, TPP>(al);
-          be = group_sum<T, TPP>(be);
+          if constexpr (std::is_same<T, dfloat>::value) {
+            al = jgroup_sum_df<TPP>(al);
+            be = jgroup_sum_df<TPP>(be);
+          } else {
+            al = group_sum<T, TPP>(al);
+            be = group_sum<T, TPP>(be);
+          }
         } else if (i >= 0) {
           al = nrm2[i];
           be = nrm2[j];
@@ -925,8 +1074,23 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           if (trivial_prev) {
             acc = Rrow[0];
           } else {
-            for (int a2 = 0; a2 < Dc; ++a2) {
-              const int a = q == 0 ? a2 : ((a2 < bc.y) ? bc.x + a2 : a2 - bc.y);
+            // the previous row's site is read from global memory: loads batched eight at a
+            // time ahead of the dependent multiply-adds (same arithmetic, same order)
+            auto col_of = [&](int a2) { return q == 0 ? a2 : ((a2 < bc.y) ? bc.x + a2 : a2 - bc.y); };
+            int a2 = 0;
+            for (; a2 + 8 <= Dc; a2 += 8) {
+              TC vb[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) vb[u] = Cp[int64_t(col_of(a2 + u)) * chi + b];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                TC v = vb[u];
+                if (((col_of(a2 + u) >= bc.x) ? 1 : 0) != pb) v *= tv;
+                dacc(acc, Rrow[a2 + u], v);
+              }
+            }
+            for (; a2 < Dc; ++a2) {
+              const int a = col_of(a2);
               TC v = Cp[int64_t(a) * chi + b];
               if (((a >= bc.x) ? 1 : 0) != pb) v *= tv;
               dacc(acc, Rrow[a2], v);
@@ -1019,7 +1183,15 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
             const TC *Qcol = qs + int64_t(q * kq) * LDA + i;
             const TC *Ucol = US + q * P::CH2 + jp;
             TC acc = 0;
-            for (int p = 0; p < kq; ++p) dacc(acc, Qcol[int64_t(p) * LDA], Ucol[p * CH]);
+            int p = 0;
+            for (; p + 8 <= kq; p += 8) {   // Q_c from global memory: loads batched ahead
+              TC qb[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) qb[u] = Qcol[int64_t(p + u) * LDA];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) dacc(acc, qb[u], Ucol[(p + u) * CH]);
+            }
+            for (; p < kq; ++p) dacc(acc, Qcol[int64_t(p) * LDA], Ucol[p * CH]);
             Th[int64_t(i) * LDT + j] = dfin(acc);
           }
           __syncthreads();
