@@ -44,10 +44,15 @@ from workloads import SAMPLING_SEED, config  # noqa: E402
 def metric_name(wl) -> str:
     return (f"accepted samples/s at L={wl.Ls[0]},chi={wl.chi} "
             "(end to end: environments + proposals + MH)")
-# Acceptance of the float64 method at the L = 256 workload, measured on the GPU (the
-# oracle computes the same method; its own MH at that size would take hours). Both
-# oracle legs (cpu_baseline and --impl reference) credit this one value.
-REF_ACCEPTANCE_L256 = 0.205
+# Acceptance of the float64-accurate method at each workload, measured on the GPU (the
+# oracle computes the same method; its own MH at these sizes would take hours). Both
+# oracle legs (cpu_baseline and --impl reference) credit this value; a workload without
+# an entry is credited acceptance 1 (an upper bound on the oracle's throughput).
+REF_ACCEPTANCE = {
+    "L256_chi64_beta3_n64_S256": 0.205,        # float64 and double-float: 0.202-0.206
+    "uneven200_L32-128_chi32_beta2": 0.997,    # mixed 0.997, double-float 0.998
+    "L1024_chi32_beta3_n64_S128": 0.034,       # double-float
+}
 # float32 instructions of one double-float multiply-add as the kernels implement it
 # (TwoProd 2, two cross-term FMAs 2, two TwoSums 12, two FastTwoSums 6, two adds 2)
 DF_FMA_OPS = 24
@@ -157,17 +162,31 @@ ORACLE_MEAN_BOND = {"L256_chi64_beta3_n64_S256": 43.31}
 def oracle_sample(wl, seconds: float = 15.0):
     """Time the FP64 oracle on a bounded sample of the workload.
 
-    Realization 0: the environment rows are built from the bottom up until
-    `seconds` have elapsed; the per-row cost of the last half of those rows is
-    extrapolated to all L rows, scaled by (D_all / D_timed)^3 where the workload's
-    all-row mean bond dimension D_all is known (ORACLE_MEAN_BOND). Proposals are not
-    timed: the environment build dominates the oracle's time, so this is an upper
-    bound on its throughput. Returns (seconds per realization, rows timed, wall s,
-    mean bond of the timed rows).
+    One realization per distinct L (the first of that size), `seconds` shared evenly
+    between them: its environment rows are built from the bottom up until its share
+    has elapsed; the per-row cost of the last half of those rows is extrapolated to all
+    L rows, scaled by (D_all / D_timed)^3 where the workload's all-row mean bond
+    dimension D_all is known (ORACLE_MEAN_BOND). The sizes' times are averaged with the
+    workload's count of each size. Proposals are not timed: the environment build
+    dominates the oracle's time, so this is an upper bound on its throughput. Returns
+    (mean seconds per realization, rows timed, wall s, mean bond of the timed rows of
+    the first size).
     """
+    t0 = time.perf_counter()
+    sizes = sorted(set(wl.Ls), key=wl.Ls.index)
+    total, rows, d0 = 0.0, 0, None
+    for L in sizes:
+        t_real, r, d = _oracle_realization(wl, wl.Ls.index(L), seconds / len(sizes))
+        total += t_real * wl.Ls.count(L)
+        rows += r
+        d0 = d if d0 is None else d0
+    return total / wl.n_real, rows, time.perf_counter() - t0, d0
+
+
+def _oracle_realization(wl, n, seconds):
     from oracle import bmps
-    L, chi, beta = wl.Ls[0], wl.chi, wl.beta
-    Jh, Jv = wl.realization(0)
+    L, chi, beta = wl.Ls[n], wl.chi, wl.beta
+    Jh, Jv = wl.realization(n)
     t0 = time.perf_counter()
     mps, lam = bmps.bottom_row_mps(Jh[L - 1], beta)
     times, dims = [], []
@@ -187,17 +206,27 @@ def oracle_sample(wl, seconds: float = 15.0):
     d_all = ORACLE_MEAN_BOND.get(wl.name)
     if d_all:
         per_row *= (d_all / d_timed) ** 3
-    return per_row * L, len(times), time.perf_counter() - t0, d_timed
+    return per_row * L, len(times), d_timed
+
+
+def ref_acceptance(args, wl):
+    if args.ref_acceptance is not None:
+        return args.ref_acceptance
+    return REF_ACCEPTANCE.get(wl.name, 1.0)
 
 
 def oracle_sample_text(wl, rows_done, d_timed, acceptance):
     d_all = ORACLE_MEAN_BOND.get(wl.name)
     scale = (f", scaled by (D_all / D_timed)^3 = ({d_all} / {d_timed:.1f})^3 for the larger bonds of "
              f"the rows above (D_all: the oracle's own full build)" if d_all else "")
-    return (f"realization 0 of {wl.name}: bottom {rows_done} environment rows timed, per-row cost "
-            f"extrapolated to all {wl.Ls[0]} rows{scale}; proposals not timed; acceptance {acceptance} "
-            f"(the float64 method's at this workload, measured on the GPU: the oracle cannot run its "
-            f"own MH at this size)")
+    sizes = sorted(set(wl.Ls))
+    which = ("realization 0" if len(sizes) == 1 else
+             f"one realization per size L in {sizes} (weighted by the count of each size)")
+    acc = (f"acceptance {acceptance} (the float64-accurate method's at this workload, measured on "
+           f"the GPU: the oracle cannot run its own MH at this size)" if wl.name in REF_ACCEPTANCE
+           else f"acceptance {acceptance} assumed (an upper bound)")
+    return (f"{which} of {wl.name}: bottom {rows_done} environment rows timed, per-row cost "
+            f"extrapolated to all rows{scale}; proposals not timed; {acc}")
 
 
 def cpu_cores():
@@ -219,9 +248,9 @@ def run_reference(args, wl):
     for _ in range(args.steps):
         t_real, rows_done, wall, d_timed = oracle_sample(wl, seconds=args.ref_seconds)
         # the oracle computes the same method; its acceptance is the method's (given)
-        vals.append(wl.S * args.ref_acceptance / t_real)
+        vals.append(wl.S * ref_acceptance(args, wl) / t_real)
     v = float(np.mean(vals))
-    sample = oracle_sample_text(wl, rows_done, d_timed, args.ref_acceptance)
+    sample = oracle_sample_text(wl, rows_done, d_timed, ref_acceptance(args, wl))
     line = {"impl": "reference", "metric": metric_name(wl), "value": v, "unit": "accepted/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -541,9 +570,10 @@ def run_ours(args, wl):
         cpu = None
         if world == 1 and args.cpu_baseline:
             t_real, rows_done, _, d_timed = oracle_sample(wl, seconds=args.ref_seconds)
-            cpu = {"value": S * args.ref_acceptance / t_real, "unit": "accepted/s", "cores": cpu_cores(),
+            acc_ref = ref_acceptance(args, wl)
+            cpu = {"value": S * acc_ref / t_real, "unit": "accepted/s", "cores": cpu_cores(),
                    "kind": "oracle",
-                   "sample": "FP64 oracle, " + oracle_sample_text(wl, rows_done, d_timed, args.ref_acceptance)}
+                   "sample": "FP64 oracle, " + oracle_sample_text(wl, rows_done, d_timed, acc_ref)}
         line = {
             "metric": metric_name(wl),
             "value": accepted_all / (my_ms_all / 1e3),
@@ -807,7 +837,8 @@ def main():
     ap.add_argument("--cutoff", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-acceptance", type=float, default=REF_ACCEPTANCE_L256)
+    ap.add_argument("--ref-acceptance", type=float, default=None,
+                    help="acceptance credited to the oracle (default: the measured value for the workload)")
     ap.add_argument("--tune-rows", type=int, default=12,
                     help="bottom rows the build autotuner times per layout (0: no autotuning)")
     ap.add_argument("--arms", default=None,

@@ -149,6 +149,10 @@ __device__ __forceinline__ void rotate(dfloat &a, dfloat &b, dfloat cs, dfloat s
   b = df::lin2(cs, bv, df::neg(sn), av);
 }
 
+// the column-norm comparison of the pivoted QR (float64, or the leading word of a double-float)
+__device__ __forceinline__ double pivot_key(double v) { return v; }
+__device__ __forceinline__ float pivot_key(dfloat v) { return v.hi; }
+
 template <typename T, int W>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
@@ -161,9 +165,9 @@ __device__ __forceinline__ T group_sum(T v) {
 // below the diagonal, their coefficients in tau. (LAPACK's geqr2 scheme:
 // beta = -sign(x0)|x|.) RS = 1 is a column-major panel, CS = 1 a row-major one.
 //
-// With PIVOT (double-float preconditioning QR) the columns are pivoted (Businger & Golub,
-// 1965: at step j the remaining column of largest norm below row j is swapped into
-// place; LAPACK's geqp3 order): piv[k] receives the original index of column k and cn
+// With PIVOT (the float64 and double-float preconditioning QR) the columns are pivoted
+// (Businger & Golub, 1965: at step j the remaining column of largest norm below row j is
+// swapped into place; LAPACK's geqp3 order): piv[k] receives the original index of column k and cn
 // holds the norms below the current row, recomputed exactly in each update pass (no
 // downdating). The triangular factor is then graded, and one-sided Jacobi on its rows
 // needs about half the sweeps (Drmac & Veselic, "New fast and accurate Jacobi SVD
@@ -174,7 +178,7 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
   const int hw = ht >> 5, lane = ht & 31;
   const int kq = min(m, n);
   if constexpr (PIVOT) {
-    static_assert(std::is_same<T, dfloat>::value, "pivoted QR is the double-float preconditioner");
+    static_assert(sizeof(T) == 8, "pivoted QR is the float64 and double-float preconditioner");
     constexpr int G = 8;
     const int grp = ht / G, gl = ht % G;
     for (int k0 = 0; k0 < n; k0 += 256 / G) {           // uniform trip count over the half
@@ -191,15 +195,16 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
     if (hw == 0) {
       if constexpr (PIVOT) {
         // the remaining column of largest norm (ties: lower index) swapped into column j
-        float best = -1.f;
+        using K = decltype(pivot_key(T()));
+        K best = K(-1);
         int bk = j;
         for (int k = j + lane; k < n; k += 32) {
-          const float v = cn[k].hi;
+          const K v = pivot_key(cn[k]);
           if (v > best) { best = v; bk = k; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const K ov = __shfl_xor_sync(0xffffffffu, best, o);
           const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
           if (ov > best || (ov == best && ok < bk)) { best = ov; bk = ok; }
         }
@@ -263,8 +268,9 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
     const T tj = tau[j];
     if (tj != T(0) || PIVOT) {   // pivoting refreshes the column norms even for a null reflector
       const T *v = A + int64_t(j) * CS;
-      if constexpr (std::is_same<T, dfloat>::value) {
-        // double-float: 8 lanes per column (32 columns at a time), 3-level reductions
+      if constexpr (std::is_same<T, dfloat>::value || PIVOT) {
+        // double-float (and pivoting): 8 lanes per column (32 columns at a time), 3-level
+        // reductions
         // (the trip count is uniform over the half: every lane reaches the shuffles)
         constexpr int G = 8;
         const int grp = ht / G, gl = ht % G;
@@ -899,9 +905,10 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   __shared__ int sh_lastrot[2];
   __shared__ int sh_keep[2 * CH];   // per candidate row: (sector << 16 | position) or -1
   __shared__ int sh_src[2 * CH];    // Jacobi row order, then kept bond index -> candidate row
-  // double-float preconditioning QR with column pivoting: per sector, the column norms and
-  // the permutation (piv: position -> original column; ipiv: original column -> position)
-  constexpr bool PIVQR = std::is_same<TC, dfloat>::value;
+  // float64 and double-float preconditioning QR with column pivoting: per sector, the column
+  // norms and the permutation (piv: position -> original column; ipiv: original column ->
+  // position)
+  constexpr bool PIVQR = sizeof(TC) == 8;
   __shared__ TC sh_cn[PIVQR ? 2 * CH : 1];
   __shared__ int sh_piv[PIVQR ? 2 * CH : 1], sh_ipiv[PIVQR ? 2 * CH : 1];
   __shared__ long long sh_key[2 * CH];   // ordering keys of the singular values
