@@ -118,11 +118,36 @@ __device__ __forceinline__ bool wait_flag(const unsigned *p, unsigned want, long
 }
 constexpr long long CLUSTER_WAIT_CYCLES = 40000000000ll;   // ~20 s at 2 GHz
 
+// Sum over a group of W lanes in double-float: a compensated reduction (each level one
+// TwoSum of the leading words, the exact error and the trailing words summed in float32,
+// renormalised at the end). Its absolute error ~ u^2 (|x_1| + ... + |x_W|) is the order of
+// the accurate double-word additions it replaces, at about half their latency; the inputs
+// may be unnormalised dot-product accumulators.
+template <int W>
+__device__ __forceinline__ dfloat jgroup_sum_df(dfloat v) {
+  float h = v.hi, l = v.lo;
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+    float s, e;
+    df::two_sum(h, oh, s, e);
+    h = s;
+    l += ol + e;
+  }
+  float s, e;
+  df::two_sum(h, l, s, e);
+  return dfloat(s, e);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
+  if constexpr (std::is_same<T, dfloat>::value) {
+    return jgroup_sum_df<32>(v);
+  } else {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
-  return v;
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+    return v;
+  }
 }
 
 // Inner-loop arithmetic, generic over the element type: plain expressions in float32
@@ -155,9 +180,13 @@ __device__ __forceinline__ float pivot_key(dfloat v) { return v.hi; }
 
 template <typename T, int W>
 __device__ __forceinline__ T group_sum(T v) {
+  if constexpr (std::is_same<T, dfloat>::value) {
+    return jgroup_sum_df<W>(v);
+  } else {
 #pragma unroll
-  for (int o = W / 2; o > 0; o >>= 1) v += shfl_xor(v, o);
-  return v;
+    for (int o = W / 2; o > 0; o >>= 1) v += shfl_xor(v, o);
+    return v;
+  }
 }
 
 // Householder QR of an m x n panel by one half of the CTA, element (i, j) at
@@ -483,28 +512,6 @@ __device__ __forceinline__ void form_q_inplace(T *A, const T *tau, int m, int kq
   else form_q_2b<T, LDA>(A, tau, m, kq, half, ht);
 }
 
-// Sum over a lane group of W lanes for the Jacobi inner products. Double-float: a
-// compensated reduction (each level one TwoSum of the leading words, the exact error
-// and the trailing words summed in float32, renormalised at the end): absolute error
-// ~ u^2 (|x_1| + ... + |x_W|), enough for the convergence test (tolerance ~ 8 sqrt(n) u^2
-// relative to |a| |b|), at about half the latency of accurate double-word additions.
-template <typename T, int W>
-__device__ __forceinline__ T jgroup_sum(T v) { return group_sum<T, W>(v); }
-template <int W>
-__device__ __forceinline__ dfloat jgroup_sum_df(dfloat v) {
-  float h = v.hi, l = v.lo;
-#pragma unroll
-  for (int o = W / 2; o > 0; o >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
-    float s, e;
-    df::two_sum(h, oh, s, e);
-    h = s;
-    l += ol + e;
-  }
-  float s, e;
-  df::two_sum(h, l, s, e);
-  return dfloat(s, e);
-}
 
 // Jacobi convergence test gamma^2 > tol^2 alpha beta. In double-float the products are
 // fourth powers of the singular values, which underflow float32's range below ~1e-10 of
