@@ -540,7 +540,9 @@ def run_ours(args, wl):
         env_avg_s = sum(env_t) / len(env_t) / 1e3
         samp_avg_s = sum(samp_t) / len(samp_t) / 1e3
         achieved = flops_env / env_avg_s / 1e9
-        if args.prec == "fp32":
+        if args.prec in ("fp32", "tf32", "bf16"):
+            # TF32 / BF16 move only the dense products to the tensor cores: the QR and Jacobi
+            # steps that bound the build stay on the float32 pipe
             peak, peak_src = peaks_alu["fp32"], "measured: cuBLAS float32 GEMM (TF32 off) on this GPU"
         elif args.prec == "dfloat":
             # a double-float multiply-add (2 flops) is DF_FMA_OPS float32 instructions on the
@@ -563,7 +565,7 @@ def run_ours(args, wl):
         # sampler: algorithmic bytes per sample-site = the right environment spilled and read
         # back (2 D values: L D values per chain do not fit on chip), the cache read once per
         # pass per realization (2 D^2 values, shared by the S chains) and the spin written
-        esz = 4 if args.prec == "fp32" else 8
+        esz = 4 if args.prec in ("fp32", "tf32", "bf16") else 8
         samp_sites = S * site_rows
         samp_bytes = samp_sites * (2.0 * dmean * esz + 2.0 * dmean * dmean * esz / S + 1.0)
         hbm_peak = peaks.get("hbm_gbs") or 6484.6
@@ -582,6 +584,8 @@ def run_ours(args, wl):
             "ms_per_step": my_ms_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f64 build + f32 sampling",
+                      "tf32": "f32 (tensor-core products from tf32 operands)",
+                      "bf16": "f32 (tensor-core products from bf16 operands)",
                       "dfloat": "f32x2 (double-float)"}[args.prec],
             "data": ("synthetic Gaussian N(0,1) disorder, seeded" if wl.kind == "gauss"
                      else "synthetic +-J disorder (p = 1/2), seeded"),
@@ -832,7 +836,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", choices=["fp64", "fp32", "mixed", "dfloat"], default="fp32")
+    ap.add_argument("--prec", choices=["fp64", "fp32", "tf32", "bf16", "mixed", "dfloat"], default="fp32")
     ap.add_argument("--workload", default="L256")
     ap.add_argument("--cutoff", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -66,8 +66,16 @@ typedef enum {
 typedef enum {
   TNMC_FP64 = 0,   /* all tensor arithmetic and the cache in float64 */
   TNMC_FP32 = 1,   /* all tensor arithmetic and the cache in float32 */
-  TNMC_TF32 = 2,   /* reserved: tensor-core TF32 contractions */
-  TNMC_BF16 = 3,   /* reserved: tensor-core BF16 contractions */
+  TNMC_TF32 = 2,   /* float32 build, cache and sampling as TNMC_FP32, with the build's two
+                      dense products per site (the previous row's site times the carried
+                      triangular factor, Sec. 3.2's MPO x MPS contraction in parity form, and
+                      the SVD input Q x blockdiag(U S)) on the tensor cores: operands rounded
+                      to TF32 (10 mantissa bits), float32 accumulation; every row normalised
+                      into the float64 log scale. Default cutoff 1e-6, as TNMC_FP32: the two
+                      modes differ only in the rounding of the products. Accurate at small
+                      beta only; the errors against the float64 oracle are tabulated by
+                      tests/test_gpu_precision_table.py */
+  TNMC_BF16 = 3,   /* as TNMC_TF32 with BF16 operands (7 mantissa bits) */
   TNMC_MIXED = 4,  /* float64 environment build (QR / SVD truncation, carried between
                       rows in float64), float32 cache and float32 sampling contractions */
   TNMC_DFLOAT = 5  /* double-float arithmetic (a float32 pair hi + lo, 48 significant bits,
@@ -94,7 +102,7 @@ typedef struct {
                             truncation threshold): at each bond keep the chi largest
                             singular values that exceed cutoff * (largest). <= 0 selects
                             the default of the precision: 1e-12 (FP64, MIXED, DFLOAT),
-                            1e-6 (FP32).
+                            1e-6 (FP32, TF32, BF16).
                             Numerically-zero singular values must be dropped: their
                             noise directions grow under the next rows' transfer MPOs. */
   int32_t ckpt_every;    /* 0: cache the environment of every row. K >= 2: cache only rows

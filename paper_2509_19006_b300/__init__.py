@@ -195,7 +195,8 @@ class ChainState:
 class TNMC:
     """A handle on the library for one batch of realizations on one CUDA device."""
 
-    DEFAULT_CUTOFF = {TNMC_FP64: 1e-12, TNMC_FP32: 1e-6, TNMC_MIXED: 1e-12, TNMC_DFLOAT: 1e-12}
+    DEFAULT_CUTOFF = {TNMC_FP64: 1e-12, TNMC_FP32: 1e-6, TNMC_MIXED: 1e-12, TNMC_DFLOAT: 1e-12,
+                      TNMC_TF32: 1e-6, TNMC_BF16: 1e-6}
 
     def __init__(self, Ls: Sequence[int], chi: int, beta: float, prec: str | int = "fp32",
                  max_samples: int = 256, device="cuda:0", stream=None, cutoff: float = 0.0,

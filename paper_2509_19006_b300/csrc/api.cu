@@ -65,25 +65,30 @@ tnmc_status check_cfg(const tnmc_config *cfg) {
   if (cfg->max_samples < 1 || cfg->max_samples > (1 << 24)) return TNMC_ERR_ARG;
   if (!std::isfinite(cfg->cutoff) || cfg->cutoff >= 1.0) return TNMC_ERR_ARG;
   if (cfg->ckpt_every < 0 || cfg->ckpt_every == 1) return TNMC_ERR_ARG;
-  if (cfg->prec == TNMC_TF32 || cfg->prec == TNMC_BF16) return TNMC_ERR_UNSUPPORTED;
-  if (cfg->prec != TNMC_FP64 && cfg->prec != TNMC_FP32 && cfg->prec != TNMC_MIXED &&
-      cfg->prec != TNMC_DFLOAT)
-    return TNMC_ERR_ARG;
+  if (cfg->prec < TNMC_FP64 || cfg->prec > TNMC_DFLOAT) return TNMC_ERR_ARG;
   for (int n = 0; n < cfg->n_real; ++n)
     if (cfg->L[n] < 1 || cfg->L[n] > kMaxL) return TNMC_ERR_ARG;
   return TNMC_OK;
 }
 
-// 0: float64 build + float64 cache; 1: float32 build + cache; 2: float64 build, float32 cache;
-// 3: double-float build + cache
+// 0: float64 build + float64 cache; 1: float32 build + cache (FP32, and TF32 / BF16 with the
+// dense products on the tensor cores); 2: float64 build, float32 cache; 3: double-float build + cache
 int env_mode(int prec) {
-  return prec == TNMC_FP64 ? 0 : (prec == TNMC_FP32 ? 1 : (prec == TNMC_DFLOAT ? 3 : 2));
+  if (prec == TNMC_FP64) return 0;
+  if (prec == TNMC_FP32 || prec == TNMC_TF32 || prec == TNMC_BF16) return 1;
+  return prec == TNMC_DFLOAT ? 3 : 2;
 }
+// operand rounding of the build's dense products (env_build.cu, TCMODE_*)
+int tc_mode_of(int prec) { return prec == TNMC_TF32 ? 1 : (prec == TNMC_BF16 ? 2 : 0); }
 // type of the cache and of the sampler: 0 = float64, 1 = float32, 2 = double-float
 int cache_code(int prec) { return prec == TNMC_FP64 ? 0 : (prec == TNMC_DFLOAT ? 2 : 1); }
 // bytes of a cache / sampler value
 int64_t value_bytes(int prec) { return cache_code(prec) == 1 ? 4 : 8; }
-double default_cutoff(int prec) { return prec == TNMC_FP32 ? 1e-6 : 1e-12; }
+// the float32 modes (FP32, TF32, BF16) share float32's cutoff: their truncations differ only
+// in the rounding of the products
+double default_cutoff(int prec) {
+  return (prec == TNMC_FP32 || prec == TNMC_TF32 || prec == TNMC_BF16) ? 1e-6 : 1e-12;
+}
 
 Plan make_plan(const tnmc_config *cfg) {
   Plan p;
@@ -258,6 +263,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
   lay.wait_cycles = 0;
   lay.variant = 0;
   lay.tune_rows = 0;
+  lay.tc_mode = tc_mode_of(cfg->prec);
   lay.ckpt64 = p.sum_ckpt > 0 ? reinterpret_cast<double *>(ws + p.off_ckpt64) : nullptr;
   lay.bonds = reinterpret_cast<int2 *>(ws + p.off_bonds);
   lay.lam = reinterpret_cast<double *>(ws + p.off_lam);

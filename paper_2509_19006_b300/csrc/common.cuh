@@ -55,6 +55,8 @@ struct Layout {
   int64_t wait_cycles;       // budget of a bounded device wait (0: the kernel's default)
   int32_t variant;           // kernel layout of the environment build (env_build.cu, VARIANT_*)
   int32_t tune_rows;         // > 0: build only each realization's bottom tune_rows rows (timing)
+  int32_t tc_mode;           // float32 build: the dense products on the tensor cores from TF32
+                             // (1) or BF16 (2) operands, float32 accumulation; 0: CUDA cores
   double *ckpt64;            // MIXED with checkpoints: the checkpoint rows in float64, or null
   int2 *bonds;               // [sum L (L+1)]: (even, odd) dimension of bond b of row r
   double *lam;               // [sum L]: log scale lambda_r of row r

@@ -31,6 +31,7 @@
 // rows, keeping every K-th row, or one K-row segment from the checkpoint below
 // it (Layout::seg_begin, seg_end); see cache_slot in common.cuh.
 #include "common.cuh"
+#include "tcmma.cuh"
 
 #include <type_traits>
 
@@ -901,6 +902,84 @@ __device__ __forceinline__ double log_cosh(double x) {
 }
 
 // TC: arithmetic of the build (and the carry between rows); TS: cache storage.
+// ---- the TF32 / BF16 contraction modes of the float32 build: the two dense products of
+// a site on the tensor cores (tcmma.cuh), each operand rounded to TF32 or BF16 as it is
+// loaded, float32 accumulation. Rows are already normalised by the row's log scale (the
+// factors removed from R and U S go into lambda_r), so the products stay in range.
+//
+// Phase A: Y_q = R_q x Ct (sector q's rows), the same operands, rows and panel writes as
+// the CUDA-core loop of the kernel. Tiles of 16 rows x 8 columns, dealt to the warps.
+template <int MODE, int CH>
+__device__ void mpo_product_tc(const float *Rb, const float *Cp, int chi, int k0, int k1, int2 bc,
+                               int2 bn, float tv, float th, bool last, float *Ab, float *Th, int warp,
+                               int lane) {
+  constexpr int LDA = 2 * CH, LDT = 2 * CH + 1;
+  constexpr int64_t CH2 = int64_t(CH) * CH;
+  const int Dc = bc.x + bc.y, Dn = bn.x + bn.y;
+  const int mt0 = (k0 + 15) >> 4, mt1 = (k1 + 15) >> 4, ntn = (Dn + 7) >> 3;
+  const int ntile = (mt0 + mt1) * ntn;
+  const int g = lane >> 2, t = lane & 3;
+  for (int tile = warp; tile < ntile; tile += ENV_THREADS / 32) {   // uniform over the warp
+    const int mtq = tile / ntn, nt = tile - mtq * ntn;
+    const int q = mtq >= mt0 ? 1 : 0;
+    const int kq = q ? k1 : k0;
+    const int i0 = (q ? mtq - mt0 : mtq) * 16;
+    const float *Rq = Rb + q * CH2;
+    auto A = [&](int i, int a2) { return (i < kq && a2 < Dc) ? Rq[i * CH + a2] : 0.f; };
+    auto B = [&](int a2, int b) {
+      if (a2 >= Dc || b >= Dn) return 0.f;
+      const int a = q == 0 ? a2 : ((a2 < bc.y) ? bc.x + a2 : a2 - bc.y);
+      const float v = Cp[int64_t(a) * chi + b];
+      return ((a >= bc.x) != (b >= bn.x)) ? v * tv : v;
+    };
+    float c[4];
+    tc_tile<MODE>(c, Dc, i0, nt * 8, lane, A, B);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int il = i0 + g + ((u & 2) ? 8 : 0), b = nt * 8 + 2 * t + (u & 1);
+      if (il >= kq || b >= Dn) continue;
+      const int i = (q ? k0 : 0) + il;
+      if (!last) {
+        const int pb = b >= bn.x ? 1 : 0;
+        const int pos0 = pb ? b - bn.x : b, pos1 = pb ? b : bn.y + b;
+        Ab[pb * (LDA * CH) + int64_t(pos0) * LDA + i] = c[u];
+        Ab[(1 - pb) * (LDA * CH) + int64_t(pos1) * LDA + i] = th * c[u];
+      } else {
+        Th[int64_t(i) * LDT] = c[u];
+      }
+    }
+  }
+}
+
+// Phase B: Theta = Q_c x blockdiag(US_0, US_1), Q_c (m x 2 kq, column-major, ld 2 CH)
+// from the slot scratch; the column tiles of each sector use that sector's block.
+template <int MODE, int CH>
+__device__ void theta_product_tc(const float *qs, const float *US, int m, int kq, int curE, int curO,
+                                 float *Th, int warp, int lane) {
+  constexpr int LDA = 2 * CH, LDT = 2 * CH + 1;
+  constexpr int64_t CH2 = int64_t(CH) * CH;
+  const int mtn = (m + 15) >> 4, nt0 = (curE + 7) >> 3, nt1 = (curO + 7) >> 3;
+  const int ntile = mtn * (nt0 + nt1);
+  const int g = lane >> 2, t = lane & 3;
+  for (int tile = warp; tile < ntile; tile += ENV_THREADS / 32) {   // uniform over the warp
+    const int mt = tile / (nt0 + nt1), ntq = tile - mt * (nt0 + nt1);
+    const int q = ntq >= nt0 ? 1 : 0;
+    const int Nq = q ? curO : curE;
+    const int n0 = (q ? ntq - nt0 : ntq) * 8;
+    const float *Qq = qs + int64_t(q * kq) * LDA;
+    const float *Uq = US + q * CH2;
+    auto A = [&](int i, int p) { return (i < m && p < kq) ? Qq[int64_t(p) * LDA + i] : 0.f; };
+    auto B = [&](int p, int jp) { return (p < kq && jp < Nq) ? Uq[p * CH + jp] : 0.f; };
+    float c[4];
+    tc_tile<MODE>(c, kq, mt * 16, n0, lane, A, B);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = mt * 16 + g + ((u & 2) ? 8 : 0), jp = n0 + 2 * t + (u & 1);
+      if (i < m && jp < Nq) Th[int64_t(i) * LDT + (q ? curE : 0) + jp] = c[u];
+    }
+  }
+}
+
 template <typename TC, typename TS, int CH, bool SPLIT>
 __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   using P = EnvPlan<TC, TS, CH>;
@@ -1078,7 +1157,17 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         // Y_q = R_q x Ct[rows in sector-q order], Ct = previous site with its
         // odd-parity blocks scaled by t_v; scattered into the two QR panels
         const int k0 = sh_kap0, k1 = sh_kap1, m = k0 + k1;
-        for (int e = tid; e < m * Dn; e += ENV_THREADS) {
+        bool on_tc = false;   // the TF32 / BF16 modes: this product on the tensor cores
+        if constexpr (std::is_same<TC, float>::value) {
+          if (lay.tc_mode != TCMODE_NONE && !trivial_prev) {
+            if (lay.tc_mode == TCMODE_TF32)
+              mpo_product_tc<TCMODE_TF32, CH>(Rb, Cp, chi, k0, k1, bc, bn, tv, th, c == L - 1, Ab, Th, warp, lane);
+            else
+              mpo_product_tc<TCMODE_BF16, CH>(Rb, Cp, chi, k0, k1, bc, bn, tv, th, c == L - 1, Ab, Th, warp, lane);
+            on_tc = true;
+          }
+        }
+        for (int e = on_tc ? m * Dn : tid; e < m * Dn; e += ENV_THREADS) {
           const int i = e / Dn, b = e % Dn;
           const int q = (i >= k0) ? 1 : 0;
           const int ip = q ? i - k0 : i;
@@ -1191,7 +1280,17 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           // Theta = Q_c x blockdiag(US_0, US_1); Q_c streamed from the slot scratch
           const int kq = inf.z;
           const TC *qs = Qstore + int64_t(c) * LDA * LDA;
-          for (int e = tid; e < m * N; e += ENV_THREADS) {
+          bool on_tc = false;   // the TF32 / BF16 modes: this product on the tensor cores
+          if constexpr (std::is_same<TC, float>::value) {
+            if (lay.tc_mode != TCMODE_NONE) {
+              if (lay.tc_mode == TCMODE_TF32)
+                theta_product_tc<TCMODE_TF32, CH>(qs, US, m, kq, curE, curO, Th, warp, lane);
+              else
+                theta_product_tc<TCMODE_BF16, CH>(qs, US, m, kq, curE, curO, Th, warp, lane);
+              on_tc = true;
+            }
+          }
+          for (int e = on_tc ? m * N : tid; e < m * N; e += ENV_THREADS) {
             const int i = e / N, j = e % N;
             const int q = (j >= curE) ? 1 : 0, jp = q ? j - curE : j;
             const TC *Qcol = qs + int64_t(q * kq) * LDA + i;

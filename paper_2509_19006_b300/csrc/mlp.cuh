@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tcmma.cuh"
 
 namespace tnmc {
 
@@ -64,21 +65,6 @@ __device__ __forceinline__ float clamp_logit(float x) {
 __device__ __forceinline__ float mlp_act(float z) {
   const float q = 0.25f * (z + 1.f) * (z + 1.f);
   return z >= 1.f ? z : (z <= -1.f ? 0.f : q);
-}
-
-// bfloat16 pair (lo in bits 0..15, hi in 16..31), each rounded to nearest even.
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16_16816(float d[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                               uint32_t a3, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // Delta of 16 rows by one warp. Lane (g = lane / 4, t = lane % 4) passes the

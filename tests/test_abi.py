@@ -61,10 +61,10 @@ def test_argument_checks(P, args):
     assert e.value.status == 1
 
 
-def test_reserved_precisions_unsupported(P):
-    with pytest.raises(P.TnmcError) as e:
-        P.workspace_size([16], 4, 1.0, P.TNMC_BF16, 4)
-    assert e.value.status == 7
+def test_tensor_core_precisions_size_like_float32(P):
+    # TF32 / BF16 round the build's products only: cache, scratch and workspace are float32's
+    for prec in (P.TNMC_TF32, P.TNMC_BF16):
+        assert P.workspace_size([16, 9], 8, 1.0, prec, 4) == P.workspace_size([16, 9], 8, 1.0, P.TNMC_FP32, 4)
 
 
 def test_status_strings(P):

@@ -251,8 +251,6 @@ def test_bad_couplings_flagged(P):
 def test_argument_errors(P):
     with pytest.raises(P.TnmcError):
         P.TNMC([8], 65, 1.0, "fp32", max_samples=4)           # chi > 64
-    with pytest.raises(P.TnmcError):
-        P.TNMC([8], 4, 1.0, "bf16", max_samples=4)            # not implemented
     t = P.TNMC([8], 4, 1.0, "fp32", max_samples=4)
     with pytest.raises(P.TnmcError) as e:
         t.propose(2, 1)                                       # before build

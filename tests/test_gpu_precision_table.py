@@ -24,7 +24,8 @@ import parity  # noqa: E402
 
 LS, CHI, S = [32] * 4, 32, 64
 # (mode, beta) -> (bound on |d log Z| / L^2, bound on |d log q|); None: recorded only.
-# The targets are |d log Z| / L^2 <= 1e-6 and |d log q| <= 1e-4. float32 sampling
+# The targets are |d log Z| / L^2 <= 1e-6 and |d log q| <= 1e-4 (TF32 and BF16 meet neither:
+# their bounds below record the errors of the rounded products). float32 sampling
 # contractions (FP32, MIXED) miss the log q target beyond beta = 1 and float32 builds
 # miss the log Z one beyond beta = 1 on some instances (see test_gpu_chi64.py); the
 # bounds below are the ones each mode meets.
@@ -32,6 +33,11 @@ BOUNDS = {
     ("fp32", 1.0): (1e-6, 1e-3), ("fp32", 2.0): None, ("fp32", 3.0): None,
     ("mixed", 1.0): (1e-6, 1e-4), ("mixed", 2.0): (1e-6, 1e-2), ("mixed", 3.0): (1e-6, None),
     ("dfloat", 1.0): (1e-6, 1e-4), ("dfloat", 2.0): (1e-6, 1e-4), ("dfloat", 3.0): (1e-6, 1e-4),
+    # tensor-core products from TF32 / BF16 operands: about 4x the measured errors (log Z per
+    # site 2.3e-5 / 5.0e-4 / 1.6e-2 in TF32, 3.9e-4 / 4.4e-3 / 6.9e-2 in BF16 at beta = 1 / 2 / 3);
+    # their sampling loses the conditionals beyond beta = 1 (log q recorded only)
+    ("tf32", 1.0): (1e-4, 1.0), ("tf32", 2.0): (2e-3, None), ("tf32", 3.0): (7e-2, None),
+    ("bf16", 1.0): (2e-3, 10.0), ("bf16", 2.0): (2e-2, None), ("bf16", 3.0): (0.3, None),
 }
 
 
@@ -89,9 +95,9 @@ def test_precision_against_oracle(P, mode, beta):
     if out:
         with open(out, "a") as f:
             f.write(json.dumps(row) + "\n")
-    assert np.isfinite(dz)
     b = BOUNDS[(mode, beta)]
     if b is not None:
+        assert np.isfinite(dz), row
         assert dz <= b[0], row
         if b[1] is not None:
             assert dq <= b[1], row

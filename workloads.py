@@ -100,6 +100,10 @@ def config(name: str) -> Workload:
         return Workload("gauss_L128_chi8_beta2_n128", [128] * 128, 2.0, 8, 256, kind="gauss")
     if name == "L1024":      # 64 +-J realizations, L=1024, beta=3, chi=32, S=128
         return Workload("L1024_chi32_beta3_n64_S128", [1024] * 64, 3.0, 32, 128)
+    if name == "paper":      # the paper's own configuration (Sec. 4): L=1024, beta=1, chi=8
+        return Workload("paper_L1024_chi8_beta1_n64_S256", [1024] * 64, 1.0, 8, 256)
+    if name == "L128b1x8":   # 8 realizations at L=128, beta=1, chi=32 (captures of the TF32 / BF16 builds)
+        return Workload("L128_chi32_beta1_n8_S64", [128] * 8, 1.0, 32, 64)
     # small cases of the L=256 workload's kernels (same beta, chi), for profiler captures
     if name == "L128x8":
         return Workload("L128_chi64_beta3_n8_S256", [128] * 8, 3.0, 64, 256)
