@@ -372,7 +372,10 @@ tnmc_status tnmc_set_realization_ids(tnmc_handle *h, const int64_t *h_ids);
  *     row pair on half the CTA; double-float: 16 lanes on the whole CTA), 1 = 8 lanes
  *     on the whole CTA, 2 = 8 lanes on half the CTA (3 is invalid);
  *   bit 2 (4): one CTA per realization even where pairs of CTAs fit;
- *   bit 3 (8): in the one-CTA build, 8 lanes per row pair instead of 4.
+ *   bit 3 (8): in the one-CTA build, 8 lanes per row pair instead of 4;
+ *   bit 4 (16): the float32 build (TNMC_FP32, TF32, BF16) on pairs of CTAs where they
+ *     fit, its Jacobi chosen by bits 0-1 (0 = 16 lanes on the whole CTA); without it the
+ *     float32 build runs one CTA per realization.
  * Applies to later tnmc_build_envs calls (and the segment rebuilds of checkpointed
  * handles). Errors: TNMC_ERR_ARG. */
 tnmc_status tnmc_set_build_variant(tnmc_handle *h, int32_t variant);

@@ -343,7 +343,7 @@ tnmc_status tnmc_set_realization_ids(tnmc_handle *h, const int64_t *h_ids) {
 }
 
 tnmc_status tnmc_set_build_variant(tnmc_handle *h, int32_t variant) {
-  if (!h || variant < 0 || variant > 15 || (variant & 3) == 3) return TNMC_ERR_ARG;
+  if (!h || variant < 0 || variant > 31 || (variant & 3) == 3) return TNMC_ERR_ARG;
   h->lay.variant = variant;
   return TNMC_OK;
 }
@@ -356,6 +356,7 @@ tnmc_status tnmc_autotune_build(tnmc_handle *h, const float *d_J, int32_t rows, 
   // candidate layouts of this precision (env_build.cu, VARIANT_*)
   std::vector<int32_t> cand;
   if (h->env_code == 0 || h->env_code == 3) cand = {0, 1, 2, 4, 4 | 8};
+  else if (h->env_code == 1) cand = {0, 8, 16, 16 | 1, 16 | 2};   // one CTA, or pairs (bit 4)
   else cand = {0, 8};
   cudaError_t e = launch_ingest(h->lay, d_J, h->stream);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

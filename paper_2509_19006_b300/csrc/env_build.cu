@@ -876,9 +876,12 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
 //     2 = 8 lanes on half the CTA;
 //   bit 2, one CTA per realization even where CTA pairs fit;
 //   bit 3, Jacobi of the one-CTA build (both sectors, one per half): 0 = 4 lanes per
-//     row pair, 1 = 8 lanes.
+//     row pair, 1 = 8 lanes;
+//   bit 4, float32 build (FP32, TF32, BF16) on pairs of CTAs where they fit (float32's
+//     default is one CTA per realization); bits 0-1 then choose its Jacobi as above
+//     (0 = 16 lanes on the whole CTA).
 // Every layout computes the same method; they differ in summation order only.
-enum : int32_t { VARIANT_PAIR_MASK = 3, VARIANT_ONE_CTA = 4, VARIANT_SINGLE_8 = 8 };
+enum : int32_t { VARIANT_PAIR_MASK = 3, VARIANT_ONE_CTA = 4, VARIANT_SINGLE_8 = 8, VARIANT_FP32_PAIRS = 16 };
 
 template <typename TC>
 __device__ __forceinline__ int jacobi_in_pair(int variant, TC *B, int nr, int nc, int nu, int ldb, int tid,
@@ -1687,17 +1690,18 @@ static cudaError_t launch_env_ts(const Layout &lay, int CH, bool split, cudaStre
   return cudaErrorInvalidValue;
 }
 
-// The float64 build runs as CTA pairs (one SM per parity sector's Jacobi) when
-// the pairs of all realizations fit on the GPU at once (2 x realizations <= SMs;
-// 74 pairs on a 148-SM B300).
+// The float64 and double-float builds run as CTA pairs (one SM per parity sector's
+// Jacobi) when the pairs of all realizations fit on the GPU at once (2 x realizations
+// <= SMs; 74 pairs on a 148-SM B300); the float32 build does so when its layout asks.
 cudaError_t launch_env_build(const Layout &lay, int mode, int CH, cudaStream_t st) {
-  if (mode == 0 || mode == 3) {
+  if (mode == 0 || mode == 3 || (mode == 1 && (lay.variant & VARIANT_FP32_PAIRS))) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const bool pairs = 2 * lay.env_slots <= sms && !(lay.variant & VARIANT_ONE_CTA);
     if (mode == 3) return launch_env_ts<dfloat, dfloat>(lay, CH, pairs, st);
+    if (mode == 1) return launch_env_ts<float, float>(lay, CH, pairs, st);
     return launch_env_ts<double, double>(lay, CH, pairs, st);
   }
   if (mode == 1) return launch_env_ts<float, float>(lay, CH, false, st);

@@ -16,6 +16,7 @@ from oracle import bmps  # noqa: E402
 import parity  # noqa: E402
 
 CANDIDATES = [0, 1, 2, 4, 12]
+CANDIDATES_FP32 = [0, 8, 16, 17, 18]   # one CTA (4 or 8 lanes), or pairs of CTAs (bit 4)
 
 
 @pytest.fixture(scope="module")
@@ -53,9 +54,32 @@ def test_every_layout_matches_the_oracle(P, prec, variant):
         assert nbd <= 1
 
 
+@pytest.mark.parametrize("variant", CANDIDATES_FP32)
+def test_every_float32_layout_matches_the_oracle(P, variant):
+    # float32: |d log Z| / L^2 <= 1e-6 (where cut gaps are wide, beta = 1) and every draw the
+    # oracle's outside the float32 band; the pair layouts move sector 1's Jacobi to a second SM
+    Ls, chi, beta, S = [9, 6, 12, 16], 8, 1.0, 40
+    reals = parity.realizations(Ls, "pmj")
+    t = P.TNMC(Ls, chi, beta, "fp32", max_samples=S)
+    t.set_build_variant(variant)
+    t.build_envs(torch.from_numpy(parity.packed_J(reals)).cuda())
+    lz = t.log_z().cpu().numpy()
+    props = t.propose(S, 42, 0)
+    torch.cuda.synchronize()
+    st, flags = t.device_status()
+    assert st == 0 and not flags.any()
+    envs = parity.oracle_envs(reals, beta, chi, t.cutoff)
+    spins = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
+    for n, ((Jh, Jv), rows) in enumerate(zip(reals, envs)):
+        L = Ls[n]
+        assert abs(lz[n] - bmps.log_z(rows)) / (L * L) <= 1e-6, (n, variant)
+        parity.compare_proposals(rows, Jh, Jv, beta, 42, 0, n, spins[n], props.logq.cpu().numpy()[n],
+                                 props.E.cpu().numpy()[n], band=2e-3, lq_atol=1e-2)
+
+
 def test_bad_layout_refused(P):
     t = P.TNMC([4], 4, 1.0, "fp64", max_samples=4)
-    for bad in (3, -1, 16):
+    for bad in (3, -1, 32, 19):
         with pytest.raises(P.TnmcError):
             t.set_build_variant(bad)
 
