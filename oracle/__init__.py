@@ -19,6 +19,9 @@ What it computes is the method itself, step by step, in float64 numpy:
                 both sides implement from its published definition.
 * ``exact``   - brute-force enumeration (Eq. 2-4) and the exact row transfer
                 matrix, the references the oracle is pinned against.
+* ``potts``   - the q-state Potts extension (Sec. 5): energy, q-state copy-tensor
+                MPOs through the same compression, q-way proposals and scores, and
+                its exact references (enumeration, row transfer matrix).
 
 Each function's docstring states how it reads the points the paper leaves open.
 """

@@ -107,13 +107,15 @@ def row_mpo(Jh_row: np.ndarray, Jv_row: np.ndarray, beta: float):
 
 
 def multiply(mpo: List[np.ndarray], mps: List[np.ndarray]) -> List[np.ndarray]:
-    """Fig. 2: MPO x MPS; new[(a, a'), s, (b, b')] = sum_n W[a, s, b, n] A[a', n, b']."""
+    """Fig. 2: MPO x MPS; new[(a, a'), s, (b, b')] = sum_n W[a, s, b, n] A[a', n, b'].
+
+    The physical dimension d is read from the tensors (2 for Ising spins, q for Potts)."""
     out = []
     for W, A in zip(mpo, mps):
         T = np.einsum("asbn,xny->axsby", W, A)
         Dl = W.shape[0] * A.shape[0]
         Dr = W.shape[2] * A.shape[2]
-        out.append(T.reshape(Dl, 2, Dr))
+        out.append(T.reshape(Dl, W.shape[1], Dr))
     return out
 
 
@@ -124,7 +126,7 @@ def compress(mps: List[np.ndarray], chi: int, cutoff: float = DEFAULT_CUTOFF):
     """Bring every bond to at most chi (Sec. 2.2, Sec. 3.2 ``compress``).
 
     1. Left-to-right QR sweep: A_c = Q R, A_c <- Q, A_{c+1} <- R A_{c+1}.
-    2. Right-to-left SVD sweep: A_c (as D_l x (2 D_r)) = U S V^T, keep the k
+    2. Right-to-left SVD sweep: A_c (as D_l x (d D_r), d the physical dimension) = U S V^T, keep the k
        largest singular values (k <= chi, S[k-1] > cutoff * S[0], k >= 1),
        A_c <- V^T[:k], A_{c-1} <- A_{c-1} U[:, :k] S[:k].
     3. Site 0 is divided by its Frobenius norm.
@@ -136,18 +138,18 @@ def compress(mps: List[np.ndarray], chi: int, cutoff: float = DEFAULT_CUTOFF):
     L = len(mps)
     log_scale = 0.0
     for c in range(L - 1):
-        Dl, _, Dr = mps[c].shape
-        Q, R = np.linalg.qr(mps[c].reshape(Dl * 2, Dr), mode="reduced")
+        Dl, d, Dr = mps[c].shape
+        Q, R = np.linalg.qr(mps[c].reshape(Dl * d, Dr), mode="reduced")
         nrm = np.linalg.norm(R)
         if nrm > 0:
             R = R / nrm
             log_scale += np.log(nrm)
-        mps[c] = Q.reshape(Dl, 2, Q.shape[1])
+        mps[c] = Q.reshape(Dl, d, Q.shape[1])
         mps[c + 1] = np.einsum("ka,asb->ksb", R, mps[c + 1])
     spectra, gaps, disc = [None] * L, [np.inf] * L, [0.0] * L
     for c in range(L - 1, 0, -1):
-        Dl, _, Dr = mps[c].shape
-        U, S, Vh = np.linalg.svd(mps[c].reshape(Dl, 2 * Dr), full_matrices=False)
+        Dl, d, Dr = mps[c].shape
+        U, S, Vh = np.linalg.svd(mps[c].reshape(Dl, d * Dr), full_matrices=False)
         k = min(chi, S.size, max(1, int(np.sum(S > cutoff * S[0]))))
         total = float(np.sum(S ** 2))
         if k < S.size:
@@ -156,7 +158,7 @@ def compress(mps: List[np.ndarray], chi: int, cutoff: float = DEFAULT_CUTOFF):
         spectra[c] = S[:k] / S[0] if S[0] > 0 else S[:k]
         s_max = S[0] if S[0] > 0 else 1.0
         log_scale += np.log(s_max)
-        mps[c] = Vh[:k].reshape(k, 2, Dr)
+        mps[c] = Vh[:k].reshape(k, d, Dr)
         mps[c - 1] = np.einsum("asb,bk->ask", mps[c - 1], U[:, :k] * (S[:k] / s_max))
     nrm = np.linalg.norm(mps[0])
     mps[0] = mps[0] / nrm
