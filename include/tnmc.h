@@ -113,6 +113,16 @@ typedef struct {
                             about one more environment build per call. Results are the same
                             bits as with 0. With TNMC_MIXED the checkpoint rows are also kept
                             in float64 (the precision the build carries between rows). */
+  int32_t q_states;      /* 0 or 2: the Ising model of Eq. 1 (every mode above). 3 or 4: the
+                            q-state Potts extension (Sec. 5), E = -sum J_ij delta(s_i, s_j) with
+                            states 0 .. q-1 stored one byte per site; float64 only (prec =
+                            TNMC_FP64), chi <= 16 with q^2 chi <= 144, no checkpoints, no
+                            learned correction. Proposals draw the first state k with
+                            u < p_0 + ... + p_k (float64 partial sums, the site's Philox uniform).
+                            Entry points other than build_envs, log_z, propose, score,
+                            mh_init_empty and mh_step return TNMC_ERR_UNSUPPORTED for Potts
+                            handles. Other values: TNMC_ERR_ARG (q = 1, q < 0) or
+                            TNMC_ERR_UNSUPPORTED (q > 4, or a limit above). */
 } tnmc_config;
 
 typedef struct tnmc_handle tnmc_handle;

@@ -56,6 +56,7 @@ class _Config(ctypes.Structure):
         ("max_samples", ctypes.c_int32),
         ("cutoff", ctypes.c_double),
         ("ckpt_every", ctypes.c_int32),
+        ("q_states", ctypes.c_int32),
     ]
 
 
@@ -122,16 +123,16 @@ def _check(status: int, what: str):
 
 
 def _cfg(Ls: Sequence[int], chi: int, beta: float, prec: int, max_samples: int, cutoff: float = 0.0,
-         ckpt_every: int = 0):
+         ckpt_every: int = 0, q: int = 2):
     arr = (ctypes.c_int32 * len(Ls))(*[int(x) for x in Ls])
     cfg = _Config(len(Ls), ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32)), int(chi),
-                  float(beta), int(prec), int(max_samples), float(cutoff), int(ckpt_every))
+                  float(beta), int(prec), int(max_samples), float(cutoff), int(ckpt_every), int(q))
     return cfg, arr
 
 
-def workspace_size(Ls, chi, beta, prec, max_samples, cutoff=0.0, ckpt_every=0) -> int:
+def workspace_size(Ls, chi, beta, prec, max_samples, cutoff=0.0, ckpt_every=0, q=2) -> int:
     lib = load_library()
-    cfg, keep = _cfg(Ls, chi, beta, prec, max_samples, cutoff, ckpt_every)
+    cfg, keep = _cfg(Ls, chi, beta, prec, max_samples, cutoff, ckpt_every, q)
     out = ctypes.c_size_t(0)
     _check(lib.tnmc_workspace_size(ctypes.byref(cfg), ctypes.byref(out)), "tnmc_workspace_size")
     return out.value
@@ -200,7 +201,7 @@ class TNMC:
 
     def __init__(self, Ls: Sequence[int], chi: int, beta: float, prec: str | int = "fp32",
                  max_samples: int = 256, device="cuda:0", stream=None, cutoff: float = 0.0,
-                 ckpt_every: int = 0):
+                 ckpt_every: int = 0, q: int = 2):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("TNMC needs a CUDA device; there is no CPU fallback")
@@ -216,9 +217,10 @@ class TNMC:
         self.sum_L2 = sum(L * L for L in self.Ls)
         self.cutoff = float(cutoff) if cutoff > 0 else self.DEFAULT_CUTOFF.get(self.prec, 1e-6)
         self.ckpt_every = int(ckpt_every)
+        self.q = int(q)   # 2: Ising; 3 or 4: the q-state Potts extension (states 0 .. q-1 per byte)
         self.plan_ch = next((c for c in (8, 16, 32, 64) if self.chi <= c), 0)   # kernel instantiation
         self._cfg, self._cfg_keep = _cfg(self.Ls, chi, beta, self.prec, max_samples, self.cutoff,
-                                         self.ckpt_every)
+                                         self.ckpt_every, self.q)
         nbytes = ctypes.c_size_t(0)
         _check(self.lib.tnmc_workspace_size(ctypes.byref(self._cfg), ctypes.byref(nbytes)),
                "tnmc_workspace_size")

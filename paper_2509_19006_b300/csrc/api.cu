@@ -32,6 +32,13 @@ int64_t static_scratch_bytes();
 int64_t sampler_smem_bytes(int prec, int CH, int L_max);
 cudaError_t launch_mlp_features(const Layout &lay, int S, int L_max, const uint8_t *spins,
                                 const float *logits, float *feat, cudaStream_t st);
+int64_t potts_slot_bytes(int L_max);
+bool potts_supported(int q, int chi);
+int potts_scratch_ch();
+cudaError_t launch_potts_build(const Layout &lay, int q, cudaStream_t st);
+cudaError_t launch_potts_log_z(const Layout &lay, int q, double *logz, cudaStream_t st);
+cudaError_t launch_potts_sample(const Layout &lay, int q, int S, uint64_t seed, uint64_t base,
+                                const uint8_t *in, uint8_t *out, double *lq, double *E, cudaStream_t st);
 }  // namespace tnmc
 
 using namespace tnmc;
@@ -66,6 +73,11 @@ tnmc_status check_cfg(const tnmc_config *cfg) {
   if (!std::isfinite(cfg->cutoff) || cfg->cutoff >= 1.0) return TNMC_ERR_ARG;
   if (cfg->ckpt_every < 0 || cfg->ckpt_every == 1) return TNMC_ERR_ARG;
   if (cfg->prec < TNMC_FP64 || cfg->prec > TNMC_DFLOAT) return TNMC_ERR_ARG;
+  if (cfg->q_states < 0 || cfg->q_states == 1) return TNMC_ERR_ARG;
+  if (cfg->q_states > 2) {   // the q-state Potts extension: float64 kernels with fixed panel bounds
+    if (cfg->prec != TNMC_FP64 || cfg->ckpt_every != 0 || !potts_supported(cfg->q_states, cfg->chi))
+      return TNMC_ERR_UNSUPPORTED;
+  }
   for (int n = 0; n < cfg->n_real; ++n)
     if (cfg->L[n] < 1 || cfg->L[n] > kMaxL) return TNMC_ERR_ARG;
   return TNMC_OK;
@@ -90,10 +102,16 @@ double default_cutoff(int prec) {
   return (prec == TNMC_FP32 || prec == TNMC_TF32 || prec == TNMC_BF16) ? 1e-6 : 1e-12;
 }
 
+// q-state Potts handles (q_states >= 3)
+bool is_potts(const tnmc_config *cfg) { return cfg->q_states > 2; }
+
 Plan make_plan(const tnmc_config *cfg) {
   Plan p;
-  p.CH = pick_ch(cfg->chi);
+  const bool potts = is_potts(cfg);
+  p.CH = potts ? potts_scratch_ch() : pick_ch(cfg->chi);
   const int64_t esz = value_bytes(cfg->prec);
+  // a Potts site is q dense chi x chi matrices; an Ising site one parity-form matrix
+  const int64_t site_mats = potts ? cfg->q_states : 1;
   for (int n = 0; n < cfg->n_real; ++n) {
     const int64_t L = cfg->L[n];
     p.sum_L2 += L * L;
@@ -112,12 +130,12 @@ Plan make_plan(const tnmc_config *cfg) {
   p.off_counter = take(64 * 4);
   p.off_jr = take(p.sum_L2 * 4);
   p.off_jd = take(p.sum_L2 * 4);
-  p.cache_bytes = p.sum_cache * int64_t(cfg->chi) * cfg->chi * esz;
+  p.cache_bytes = p.sum_cache * site_mats * int64_t(cfg->chi) * cfg->chi * esz;
   p.off_cache = take(p.cache_bytes);
   p.off_bonds = take(p.sum_bonds * 8);
   p.off_lam = take(p.sum_L * 8);
   p.env_slots = std::min(cfg->n_real, kEnvSlots);
-  p.env_slot = env_slot_bytes(env_mode(cfg->prec), p.CH, p.L_max, cfg->chi);
+  p.env_slot = potts ? potts_slot_bytes(p.L_max) : env_slot_bytes(env_mode(cfg->prec), p.CH, p.L_max, cfg->chi);
   p.env_bytes = p.env_slot * p.env_slots;
   p.off_env = take(p.env_bytes);
   p.samp_bytes = int64_t(cfg->max_samples) * p.sum_L * p.CH * esz;
@@ -142,6 +160,7 @@ struct tnmc_handle {
   int prec_code;   // cache_code(): sampler / log Z kernels on float64 (0), float32 (1), double-float (2)
   cudaStream_t stream;
   bool built = false;
+  int q = 2;       // 2: Ising; 3 or 4: the q-state Potts extension (potts.cu)
 };
 
 namespace {
@@ -219,6 +238,7 @@ tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes, voi
   h->plan = p;
   h->env_code = env_mode(cfg->prec);
   h->prec_code = cache_code(cfg->prec);
+  h->q = is_potts(cfg) ? cfg->q_states : 2;
   h->stream = as_stream(cuda_stream);
   unsigned char *ws = static_cast<unsigned char *>(d_ws);
 
@@ -299,6 +319,7 @@ void tnmc_destroy(tnmc_handle *h) { delete h; }
 tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spectra,
                                  double *d_rowinfo) {
   if (!h) return TNMC_ERR_ARG;
+  if (h->q > 2 && (d_logits || d_spectra || d_rowinfo)) return TNMC_ERR_UNSUPPORTED;
   h->lay.dbg_logits = d_logits;
   h->lay.dbg_spectra = d_spectra;
   h->lay.dbg_rowinfo = d_rowinfo;
@@ -307,6 +328,7 @@ tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spec
 
 tnmc_status tnmc_set_correction(tnmc_handle *h, const void *d_params_bf16, int32_t enabled) {
   if (!h) return TNMC_ERR_ARG;
+  if (h->q > 2 && enabled) return TNMC_ERR_UNSUPPORTED;
   if (!enabled) {
     h->lay.mlp = nullptr;
     return TNMC_OK;
@@ -320,6 +342,7 @@ tnmc_status tnmc_mlp_features(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
                               const float *d_logits, float *d_feat) {
   if (!h || !d_spins || !d_logits || !d_feat || S < 1) return TNMC_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(d_feat) & 15) != 0) return TNMC_ERR_ARG;
+  if (h->q > 2) return TNMC_ERR_UNSUPPORTED;
   if (!h->built) return TNMC_ERR_STATE;   // the couplings are copied in by tnmc_build_envs
   return launch_mlp_features(h->lay, S, h->plan.L_max, d_spins, d_logits, d_feat, h->stream) ==
                  cudaSuccess
@@ -353,6 +376,7 @@ int32_t tnmc_get_build_variant(const tnmc_handle *h) { return h ? h->lay.variant
 tnmc_status tnmc_autotune_build(tnmc_handle *h, const float *d_J, int32_t rows, int32_t *h_variants,
                                 float *h_ms, int32_t *h_count) {
   if (!h || !d_J || rows < 1 || !h_count) return TNMC_ERR_ARG;
+  if (h->q > 2) return TNMC_ERR_UNSUPPORTED;
   // candidate layouts of this precision (env_build.cu, VARIANT_*)
   std::vector<int32_t> cand;
   if (h->env_code == 0 || h->env_code == 3) cand = {0, 1, 2, 4, 4 | 8};
@@ -400,6 +424,12 @@ tnmc_status tnmc_set_wait_budget(tnmc_handle *h, int64_t cycles) {
 tnmc_status tnmc_build_envs(tnmc_handle *h, const float *d_J) {
   if (!h || !d_J) return TNMC_ERR_ARG;
   cudaError_t e = launch_ingest(h->lay, d_J, h->stream);
+  if (h->q > 2) {
+    if (e == cudaSuccess) e = launch_potts_build(h->lay, h->q, h->stream);
+    if (e != cudaSuccess) return TNMC_ERR_CUDA;
+    h->built = true;
+    return TNMC_OK;
+  }
   if (e == cudaSuccess && h->lay.dbg_spectra)
     e = cudaMemsetAsync(h->lay.dbg_spectra, 0,
                         size_t(h->plan.sum_bonds) * h->cfg.chi * sizeof(double), h->stream);
@@ -412,6 +442,8 @@ tnmc_status tnmc_build_envs(tnmc_handle *h, const float *d_J) {
 tnmc_status tnmc_log_z(tnmc_handle *h, double *d_logz) {
   if (!h || !d_logz) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
+  if (h->q > 2)
+    return launch_potts_log_z(h->lay, h->q, d_logz, h->stream) == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
   return launch_log_z(h->lay, h->prec_code, d_logz, h->stream) == cudaSuccess ? TNMC_OK
                                                                                : TNMC_ERR_CUDA;
 }
@@ -421,6 +453,9 @@ tnmc_status tnmc_propose(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
   if (!h || !d_spins || !d_logq || !d_E) return TNMC_ERR_ARG;
   if (S < 1 || S > h->cfg.max_samples) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
+  if (h->q > 2)
+    return launch_potts_sample(h->lay, h->q, S, seed, prop_base, nullptr, d_spins, d_logq, d_E,
+                               h->stream) == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
   return for_segments(h, [&](const Layout &l) {
            return launch_propose(l, h->prec_code, h->plan.CH, S, seed, prop_base, d_spins, d_logq,
                                  d_E, h->stream);
@@ -433,6 +468,7 @@ tnmc_status tnmc_propose_static(tnmc_handle *h, int32_t S, uint64_t seed, uint64
                                 uint8_t *d_spins, double *d_logq, double *d_E) {
   if (!h || !d_spins || !d_logq || !d_E) return TNMC_ERR_ARG;
   if (S < 1) return TNMC_ERR_ARG;
+  if (h->q > 2) return TNMC_ERR_UNSUPPORTED;
   if (!h->built) return TNMC_ERR_STATE;
   bool too_big = false;
   const int64_t esz = value_bytes(h->cfg.prec);
@@ -452,6 +488,9 @@ tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins, double
   if (!h || !d_spins || !d_logq || !d_E) return TNMC_ERR_ARG;
   if (S < 1 || S > h->cfg.max_samples) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
+  if (h->q > 2)
+    return launch_potts_sample(h->lay, h->q, S, 0, 0, d_spins, nullptr, d_logq, d_E, h->stream) ==
+                   cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
   return for_segments(h, [&](const Layout &l) {
            return launch_score(l, h->prec_code, h->plan.CH, S, d_spins, d_logq, d_E, h->stream);
          }) == cudaSuccess
@@ -462,6 +501,7 @@ tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins, double
 tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
                          double *d_state_logq, double *d_state_E) {
   if (!h || !d_state_spins || !d_state_logq || !d_state_E) return TNMC_ERR_ARG;
+  if (h->q > 2) return TNMC_ERR_UNSUPPORTED;
   if (!h->built) return TNMC_ERR_STATE;
   cudaError_t e = launch_init_state(h->lay, seed, d_state_spins, h->stream);
   if (e == cudaSuccess)
@@ -475,6 +515,7 @@ tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
 tnmc_status tnmc_observables(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
                              const double *d_logq, const double *d_E, double *d_out) {
   if (!h || !d_spins || !d_logq || !d_E || !d_out || S < 1) return TNMC_ERR_ARG;
+  if (h->q > 2) return TNMC_ERR_UNSUPPORTED;
   return launch_observables(h->lay, S, d_spins, d_logq, d_E, d_out, h->stream) == cudaSuccess
              ? TNMC_OK
              : TNMC_ERR_CUDA;

@@ -1,0 +1,658 @@
+// q-state Potts extension (Sec. 5: the method carries over to Potts models with the
+// physical index of every tensor widened to q states), float64, batched over
+// realizations x samples like the Ising path:
+//   E(s) = - sum_<ij> J_ij delta(s_i, s_j),  s_i in {0 .. q-1}.
+// There is no parity form here (the Z2 symmetry of the Ising model has no q-state
+// analogue that halves the storage), so every site is a dense chi x q x chi tensor,
+// stored as A[s][a][b] (q matrices chi x chi, zero padded), and every QR and SVD runs
+// on the whole matrix.
+//
+// potts_build_kernel: one persistent 512-thread CTA per realization. For row r = L-1 .. 0
+// the row's transfer MPO (copy tensors W[a, s, b, n] = delta(a, s) Bh[s, b] Bv[s, n], with
+// the normalised Boltzmann matrices B(J)[a, b] = exp(beta J delta(a, b) - beta max(J, 0)))
+// is applied to the row below and the result compressed back to chi:
+//   phase A (sites 0 -> L-1): C[s] = sum_n Bv[s, n] A_c[n] of the row below, the carried
+//     triangular factor absorbed, T[(k, s), (b, b')] = Bh[s, b] sum_a' R[k, (s, a')] C[s][a', b'],
+//     a Householder QR of T, R normalised (its norm into lambda_r), Q kept for phase B;
+//   phase B (sites L-1 -> 0): Theta = Q_c (US) as (left bond) x (q x right bond), a one-sided
+//     Jacobi SVD on the rows of [Theta | I] (the identity block accumulates U^T), the chi
+//     largest singular values above cutoff x largest kept, V^T stored, U S / s_max carried.
+// The bottom row is the same sweep over a trivial row below (C = 1).
+//
+// potts_sample_kernel: one warp per chain, eight chains per CTA sharing the staged site
+// tensors; right environments R_c = (sum_s Bv(r-1)[s_up, s] A_{c+1}[s]) R_{c+1} spilled to
+// the sampler scratch, then the left sweep: rho_s = | l A_c[s] R_c |, p(s) proportional to
+// rho_s Bv(r-1, c)[s_up, s], the state drawn as the first k with u < p_0 + ... + p_k
+// (float64 partial sums), log q += log p_k, E += -Jh delta - Jv delta (left bond, then up).
+#include "common.cuh"
+
+namespace tnmc {
+
+namespace {
+
+constexpr int PT = 512;          // threads of the build CTA
+constexpr int PQ = 4;            // largest q
+constexpr int PCH = 16;          // largest chi
+constexpr int PD = 48;           // largest q x chi (bond of MPO x MPS)
+constexpr int PM = 144;          // largest panel rows (q x PD); q^2 chi <= 144
+constexpr int PLDT = 2 * PD + 1; // row stride of [Theta | U^T]
+constexpr int P_MAX_SWEEPS = 40;
+
+struct PottsSmem {
+  static constexpr int oA = 0;                     // panel, column-major, ld PM
+  static constexpr int oR = oA + PM * PD;          // R (row-major, ld PD)
+  static constexpr int oC = oR + PD * PD;          // C[s][a'][b'] (ld PCH)
+  static constexpr int oT = oC + PQ * PCH * PCH;   // [Theta | U^T] (ld PLDT)
+  static constexpr int oU = oT + PD * PLDT;        // U S (row-major, ld PCH)
+  static constexpr int oTau = oU + PD * PCH;
+  static constexpr int oSn = oTau + PD;
+  static constexpr int n = oSn + PD;
+  static constexpr int bytes = n * 8;
+};
+
+__device__ __forceinline__ double pwarp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// normalised Boltzmann weight of a bond: exp(beta J delta(a, b) - beta max(J, 0))
+__device__ __forceinline__ double pweight(double beta, double J, bool same) {
+  return exp(beta * J * (same ? 1.0 : 0.0) - beta * fmax(J, 0.0));
+}
+
+// Householder QR of the m x n column-major panel A (ld PM) by the whole CTA (LAPACK's
+// geqr2 scheme, beta = -sign(x0) |x|; reflectors below the diagonal with v_j = 1 implied).
+__device__ void p_householder(double *A, int m, int n, double *tau) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kq = min(m, n);
+  for (int j = 0; j < kq; ++j) {
+    double *col = A + j * PM;
+    if (warp == 0) {
+      double s2 = 0.0;
+      for (int i = j + 1 + lane; i < m; i += 32) s2 += col[i] * col[i];
+      s2 = pwarp_sum(s2);
+      const double x0 = col[j];
+      if (s2 == 0.0) {
+        if (lane == 0) tau[j] = 0.0;
+      } else {
+        const double mu = sqrt(x0 * x0 + s2);
+        const double be = x0 <= 0.0 ? mu : -mu;
+        const double sc = 1.0 / (x0 - be);
+        for (int i = j + 1 + lane; i < m; i += 32) col[i] *= sc;
+        if (lane == 0) { tau[j] = (be - x0) / be; col[j] = be; }
+      }
+    }
+    __syncthreads();
+    const double tj = tau[j];
+    if (tj != 0.0) {
+      for (int k = j + 1 + warp; k < n; k += PT / 32) {
+        double *ck = A + k * PM;
+        double w = lane == 0 ? ck[j] : 0.0;
+        for (int i = j + 1 + lane; i < m; i += 32) w += col[i] * ck[i];
+        w = pwarp_sum(w) * tj;
+        if (lane == 0) ck[j] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) ck[i] -= w * col[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Explicit Q (m x kq) in place of the reflectors (LAPACK's org2r order).
+__device__ void p_form_q(double *A, const double *tau, int m, int kq) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int j = kq - 1; j >= 0; --j) {
+    const double tj = tau[j];
+    const double *v = A + j * PM;
+    if (tj != 0.0) {
+      for (int l = j + 1 + warp; l < kq; l += PT / 32) {
+        double *ql = A + l * PM;
+        double w = lane == 0 ? ql[j] : 0.0;
+        for (int i = j + 1 + lane; i < m; i += 32) w += v[i] * ql[i];
+        w = pwarp_sum(w) * tj;
+        if (lane == 0) ql[j] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) ql[i] -= w * v[i];
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double *qj = A + j * PM;
+      for (int i = lane; i < m; i += 32) {
+        if (i < j) qj[i] = 0.0;
+        else if (i == j) qj[i] = 1.0 - tj;
+        else qj[i] = -tj * qj[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One-sided Jacobi on the nr rows of B (ld PLDT): inner products over the first nc
+// columns, rotations over nc + nu columns. Round-robin (circle) schedule, 16 lanes per
+// row pair, the three inner products measured exactly in every round. A pair is rotated
+// while |gamma| > tol sqrt(alpha beta), tol = 8 sqrt(nc) eps, unless either row is below
+// eps x the largest row (rounding noise). Returns the sweeps taken.
+__device__ int p_jacobi(double *B, int nr, int nc, int nu, int *sh_flag) {
+  const int tid = threadIdx.x;
+  if (nr <= 1) return 0;
+  constexpr int TPP = 16;
+  const int P = nr + (nr & 1), np = P / 2;
+  const int g = tid / TPP, gl = tid % TPP;
+  const double eps = 1.1102230246251565e-16;
+  const double tol2 = 64.0 * eps * eps * double(nc > 4 ? nc : 4);
+  __shared__ double sh_mx;
+  if (tid == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < nr; ++i) {
+      double s = 0.0;
+      for (int x = 0; x < nc; ++x) s += B[i * PLDT + x] * B[i * PLDT + x];
+      mx = fmax(mx, s);
+    }
+    sh_mx = mx;
+  }
+  __syncthreads();
+  const double floor2 = sh_mx * eps * eps;
+  int sweep = 0;
+  for (; sweep < P_MAX_SWEEPS; ++sweep) {
+    if (tid == 0) *sh_flag = 0;
+    __syncthreads();
+    for (int k = 0; k < P - 1; ++k) {
+      int i = -1, j = -1;
+      if (g < np) {
+        const int p0 = g, p1 = P - 1 - g;
+        i = p0 == 0 ? 0 : 1 + (p0 - 1 + k) % (P - 1);
+        j = 1 + (p1 - 1 + k) % (P - 1);
+        if (i >= nr || j >= nr) i = j = -1;
+      }
+      double al = 0.0, be = 0.0, ga = 0.0;
+      if (i >= 0) {
+        const double *a = B + i * PLDT, *b = B + j * PLDT;
+        for (int x = gl; x < nc; x += TPP) {
+          al += a[x] * a[x]; be += b[x] * b[x]; ga += a[x] * b[x];
+        }
+      }
+#pragma unroll
+      for (int o = TPP / 2; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      }
+      if (i >= 0 && al > floor2 && be > floor2 && ga * ga > tol2 * al * be) {
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        double *a = B + i * PLDT, *b = B + j * PLDT;
+        for (int x = gl; x < nc + nu; x += TPP) {
+          const double av = a[x], bv = b[x];
+          a[x] = cs * av - sn * bv;
+          b[x] = sn * av + cs * bv;
+        }
+        if (gl == 0) *sh_flag = 1;
+      }
+      __syncthreads();
+    }
+    const int rotated = *sh_flag;
+    __syncthreads();
+    if (!rotated) break;
+  }
+  return sweep + 1;
+}
+
+__global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *W = (double *)smem_raw;
+  double *Ap = W + PottsSmem::oA, *Rb = W + PottsSmem::oR, *Cs = W + PottsSmem::oC;
+  double *Th = W + PottsSmem::oT, *US = W + PottsSmem::oU, *tau = W + PottsSmem::oTau;
+  double *sn = W + PottsSmem::oSn;
+  __shared__ double sh_red[PT / 32];
+  __shared__ double sh_lam, sh_smax;
+  __shared__ int sh_n, sh_flag, sh_keep, sh_kprev;
+  __shared__ int sh_src[PD];
+  __shared__ double sh_Bh[PQ * PQ], sh_Bv[PQ * PQ];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int chi = lay.chi;
+  const int64_t chi2 = int64_t(chi) * chi;
+  const double beta = lay.beta;
+  const int64_t site_vals = int64_t(q) * chi2;
+  unsigned char *slot = (unsigned char *)lay.env_scratch + int64_t(blockIdx.x) * lay.env_slot_bytes;
+  double *Qstore = (double *)slot;                                     // L_max panels PM x PD
+  int2 *info = (int2 *)(slot + align256(int64_t(lay.L_max) * PM * PD * 8));   // (kprev, kq) per site
+
+  for (;;) {
+    if (tid == 0) sh_n = atomicAdd(lay.counter, 1);
+    __syncthreads();
+    const int idx = sh_n;
+    __syncthreads();
+    if (idx >= lay.n_real) break;
+    const int n = lay.order[idx];
+    const RealInfo ri = lay.reals[n];
+    const int L = ri.L;
+    if (lay.flags[n] & FLAG_BAD_J) continue;   // uniform
+    const float *jr = lay.jr + ri.site_off, *jd = lay.jd + ri.site_off;
+    double *cache_n = (double *)lay.cache + ri.cache_off * site_vals;
+    int2 *bonds_n = lay.bonds + ri.bond_off;
+    if (tid == 0) sh_lam = 0.0;
+    for (int r = L - 1; r >= 0; --r) {
+      const bool bottom = (r == L - 1);
+      const double *prev = bottom ? nullptr : cache_n + int64_t(r + 1) * L * site_vals;
+      const int2 *bprev = bottom ? nullptr : bonds_n + int64_t(r + 1) * (L + 1);
+      double *dst_row = cache_n + int64_t(r) * L * site_vals;
+      // row constants: the normalisations of the row's Boltzmann matrices
+      {
+        double acc = 0.0;
+        for (int c = tid; c < L; c += PT) {
+          if (c < L - 1) acc += beta * fmax((double)jr[r * L + c], 0.0);
+          if (!bottom) acc += beta * fmax((double)jd[r * L + c], 0.0);
+        }
+        acc = pwarp_sum(acc);
+        if (lane == 0) sh_red[warp] = acc;
+        __syncthreads();
+        if (tid == 0) {
+          double s = 0.0;
+          for (int w = 0; w < PT / 32; ++w) s += sh_red[w];
+          sh_lam += s;
+          sh_kprev = 1;
+          Rb[0] = 1.0;
+        }
+        __syncthreads();
+      }
+      // ===================== phase A: MPO x MPS with the carried R, QR sweep
+      for (int c = 0; c < L; ++c) {
+        const int Dl = bottom ? 1 : bprev[c].x, Dr = bottom ? 1 : bprev[c + 1].x;
+        const bool last = (c == L - 1);
+        const int Bdim = last ? 1 : q;
+        const int kprev = sh_kprev;
+        if (tid < q * q) {
+          const int a = tid / q, b = tid % q;
+          sh_Bh[tid] = last ? 1.0 : pweight(beta, (double)jr[r * L + c], a == b);
+          sh_Bv[tid] = bottom ? 0.0 : pweight(beta, (double)jd[r * L + c], a == b);
+        }
+        __syncthreads();
+        // C[s][a'][b'] = sum_n Bv[s, n] A_c[n][a'][b'] of the row below (1 on the bottom row)
+        for (int e = tid; e < q * Dl * Dr; e += PT) {
+          const int s = e / (Dl * Dr), rem = e % (Dl * Dr), a = rem / Dr, b = rem % Dr;
+          double acc;
+          if (bottom) {
+            acc = 1.0;
+          } else {
+            acc = 0.0;
+            const double *site = prev + int64_t(c) * site_vals;
+            for (int nn = 0; nn < q; ++nn) acc += sh_Bv[s * q + nn] * site[(int64_t(nn) * chi + a) * chi + b];
+          }
+          Cs[(s * PCH + a) * PCH + b] = acc;
+        }
+        __syncthreads();
+        // T[(k, s), (b, b')] = Bh[s, b] sum_a' R[k, (s, a')] C[s][a'][b'] (site 0: R = 1, a' = 0)
+        const int m = kprev * q, ncol = Bdim * Dr;
+        for (int e = tid; e < m * ncol; e += PT) {
+          const int row = e / ncol, col = e % ncol;
+          const int k = row / q, s = row % q, b = col / Dr, bb = col % Dr;
+          double acc = 0.0;
+          if (c == 0) {
+            acc = Cs[(s * PCH + 0) * PCH + bb];
+          } else {
+            const double *Rk = Rb + k * PD + s * Dl;
+            for (int a = 0; a < Dl; ++a) acc += Rk[a] * Cs[(s * PCH + a) * PCH + bb];
+          }
+          Ap[row + col * PM] = sh_Bh[s * q + b] * acc;
+        }
+        __syncthreads();
+        if (last) break;   // the last site starts phase B from the panel
+        p_householder(Ap, m, ncol, tau);
+        const int kq = min(m, ncol);
+        // R = upper trapezoid (kq x ncol), normalised
+        {
+          double acc = 0.0;
+          for (int e = tid; e < kq * ncol; e += PT) {
+            const int i = e / ncol, b = e % ncol;
+            if (b >= i) { const double v = Ap[i + b * PM]; acc += v * v; }
+          }
+          acc = pwarp_sum(acc);
+          if (lane == 0) sh_red[warp] = acc;
+          __syncthreads();
+          double nrm2 = 0.0;
+          for (int w = 0; w < PT / 32; ++w) nrm2 += sh_red[w];
+          const double nrm = sqrt(nrm2);
+          const bool ok = nrm > 0.0 && isfinite(nrm);
+          const double inv = ok ? 1.0 / nrm : 0.0;
+          for (int e = tid; e < kq * ncol; e += PT) {
+            const int i = e / ncol, b = e % ncol;
+            Rb[i * PD + b] = (b >= i) ? Ap[i + b * PM] * inv : 0.0;
+          }
+          if (tid == 0) {
+            if (ok) sh_lam += log(nrm);
+            else set_flag(lay.flags, n, FLAG_NUMERIC);
+          }
+        }
+        __syncthreads();
+        p_form_q(Ap, tau, m, kq);
+        double *qs = Qstore + int64_t(c) * PM * PD;
+        for (int e = tid; e < m * kq; e += PT) {
+          const int col = e / m, i = e % m;
+          qs[i + col * PM] = Ap[i + col * PM];
+        }
+        if (tid == 0) { info[c] = make_int2(kprev, kq); sh_kprev = kq; }
+        __syncthreads();
+      }
+      // ===================== phase B: truncating SVD sweep, right to left
+      int kr = 1;   // kept bond to the right of the current site
+      for (int c = L - 1; c >= 0; --c) {
+        const int Dl = (c == L - 1) ? sh_kprev : info[c].x;   // left bond of site c
+        const int nc = q * kr;
+        // Theta[a][(s, j)]
+        if (c == L - 1) {
+          for (int e = tid; e < Dl * q; e += PT) {
+            const int a = e / q, s = e % q;
+            Th[a * PLDT + s] = Ap[(a * q + s) + 0 * PM];
+          }
+        } else {
+          const int kq = info[c].y;
+          const double *qs = Qstore + int64_t(c) * PM * PD;
+          for (int e = tid; e < Dl * nc; e += PT) {
+            const int a = e / nc, col = e % nc, s = col / kr, j = col % kr;
+            double acc = 0.0;
+            for (int p = 0; p < kq; ++p) acc += qs[(a * q + s) + p * PM] * US[p * PCH + j];
+            Th[a * PLDT + col] = acc;
+          }
+        }
+        __syncthreads();
+        double *site_dst = dst_row + int64_t(c) * site_vals;
+        if (c == 0) {
+          // site 0 (left bond 1): divided by its norm
+          double acc = 0.0;
+          for (int x = tid; x < nc; x += PT) acc += Th[x] * Th[x];
+          acc = pwarp_sum(acc);
+          if (lane == 0) sh_red[warp] = acc;
+          __syncthreads();
+          double nrm2 = 0.0;
+          for (int w = 0; w < PT / 32; ++w) nrm2 += sh_red[w];
+          const double nrm = sqrt(nrm2);
+          const bool ok = nrm > 0.0 && isfinite(nrm);
+          const double inv = ok ? 1.0 / nrm : 0.0;
+          for (int64_t e = tid; e < site_vals; e += PT) {
+            const int s = int(e / chi2), rem = int(e % chi2), a = rem / chi, b = rem % chi;
+            site_dst[e] = (a == 0 && b < kr) ? Th[s * kr + b] * inv : 0.0;
+          }
+          if (tid == 0) {
+            if (ok) sh_lam += log(nrm);
+            else set_flag(lay.flags, n, FLAG_NUMERIC);
+            bonds_n[int64_t(r) * (L + 1) + 0] = make_int2(1, 0);
+            bonds_n[int64_t(r) * (L + 1) + L] = make_int2(1, 0);
+            if (L > 1) bonds_n[int64_t(r) * (L + 1) + 1] = make_int2(kr, 0);
+            lay.lam[ri.row_off + r] = sh_lam;
+          }
+          __syncthreads();
+          break;
+        }
+        // [Theta | I]: the rotations accumulate U^T in the identity block
+        for (int e = tid; e < Dl * Dl; e += PT) {
+          const int i = e / Dl, p = e % Dl;
+          Th[i * PLDT + nc + p] = (i == p) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        p_jacobi(Th, Dl, nc, Dl, &sh_flag);
+        // singular values = row norms; keep the chi largest above cutoff x largest
+        for (int i = tid; i < Dl; i += PT) {
+          double s2 = 0.0;
+          for (int x = 0; x < nc; ++x) s2 += Th[i * PLDT + x] * Th[i * PLDT + x];
+          sn[i] = sqrt(s2);
+        }
+        __syncthreads();
+        if (tid == 0) {
+          double mx = 0.0;
+          for (int i = 0; i < Dl; ++i) mx = fmax(mx, sn[i]);
+          sh_smax = mx;
+        }
+        __syncthreads();
+        const double smax = sh_smax, thr = smax * lay.cutoff;
+        if (tid < Dl) {
+          const int i = tid;
+          int rank = 0;
+          for (int j = 0; j < Dl; ++j) rank += (sn[j] > sn[i]) || (sn[j] == sn[i] && j < i);
+          const bool keep = rank < chi && (sn[i] > thr || rank == 0);
+          if (keep) sh_src[rank] = i;
+        }
+        if (tid == 0) {
+          int kk = 0;
+          for (int i = 0; i < Dl; ++i) {
+            int rank = 0;
+            for (int j = 0; j < Dl; ++j) rank += (sn[j] > sn[i]) || (sn[j] == sn[i] && j < i);
+            kk += (rank < chi && (sn[i] > thr || rank == 0)) ? 1 : 0;
+          }
+          sh_keep = kk;
+          if (smax > 0.0 && isfinite(smax)) sh_lam += log(smax);
+          else set_flag(lay.flags, n, FLAG_NUMERIC);
+        }
+        __syncthreads();
+        const int kk = sh_keep;
+        // cache site c: A[s][a''][j] = V^T[a''][(s, j)]
+        for (int64_t e = tid; e < site_vals; e += PT) {
+          const int s = int(e / chi2), rem = int(e % chi2), a = rem / chi, b = rem % chi;
+          double v = 0.0;
+          if (a < kk && b < kr) {
+            const int i = sh_src[a];
+            v = Th[i * PLDT + s * kr + b] / sn[i];
+          }
+          site_dst[e] = v;
+        }
+        // U S / s_max for site c - 1 (rows: the left bond of site c)
+        const double inv = smax > 0.0 ? 1.0 / smax : 0.0;
+        for (int e = tid; e < Dl * kk; e += PT) {
+          const int p = e / kk, a = e % kk;
+          const int i = sh_src[a];
+          US[p * PCH + a] = Th[i * PLDT + nc + p] * sn[i] * inv;
+        }
+        if (tid == 0) bonds_n[int64_t(r) * (L + 1) + c] = make_int2(kk, 0);
+        kr = kk;
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// log Z = lambda_0 + log sum over the top row's states (Eq. 6); one warp per realization.
+__global__ void potts_log_z_kernel(Layout lay, int q, double *logz) {
+  const int n = blockIdx.x;
+  const int lane = threadIdx.x;
+  const RealInfo ri = lay.reals[n];
+  const int L = ri.L, chi = lay.chi;
+  const int64_t chi2 = int64_t(chi) * chi, site_vals = int64_t(q) * chi2;
+  const double *row0 = (const double *)lay.cache + ri.cache_off * site_vals;
+  const int2 *b0 = lay.bonds + ri.bond_off;
+  double v = lane == 0 ? 1.0 : 0.0, lacc = 0.0;
+  for (int c = 0; c < L; ++c) {
+    const int Dl = b0[c].x, Dr = b0[c + 1].x;
+    const double *A = row0 + int64_t(c) * site_vals;
+    double acc = 0.0;
+    for (int a = 0; a < Dl; ++a) {
+      const double va = __shfl_sync(0xffffffffu, v, a);
+      if (lane < Dr)
+        for (int s = 0; s < q; ++s) acc += va * A[(int64_t(s) * chi + a) * chi + lane];
+    }
+    const double nrm = sqrt(pwarp_sum(acc * acc));
+    v = nrm > 0.0 ? acc / nrm : 0.0;
+    lacc += log(nrm);
+  }
+  if (lane == 0) {
+    const double val = lay.lam[ri.row_off] + lacc + log(fabs(v));
+    logz[n] = val;
+    if (!isfinite(val)) set_flag(lay.flags, n, FLAG_NUMERIC);
+  }
+}
+
+constexpr int PS_CHAINS = 8;   // chains (warps) per sampler CTA
+
+// Proposals (FORCED = false) or teacher-forced scores (FORCED = true) of S chains per
+// realization; one warp per chain, lane b holds column b of the chain's vectors.
+template <bool FORCED>
+__global__ void __launch_bounds__(32 * PS_CHAINS) potts_sample_kernel(
+    Layout lay, int q, int S, uint64_t seed, uint64_t prop_base, const uint8_t *in_states,
+    uint8_t *out_states, double *out_logq, double *out_E) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *As = (double *)smem_raw;   // q x chi x chi of the current site
+  const int bpr = (S + PS_CHAINS - 1) / PS_CHAINS;
+  const int n = blockIdx.x / bpr;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sid = (blockIdx.x % bpr) * PS_CHAINS + warp;
+  const bool act = sid < S;
+  const RealInfo ri = lay.reals[n];
+  const int L = ri.L, chi = lay.chi;
+  const int64_t chi2 = int64_t(chi) * chi, site_vals = int64_t(q) * chi2;
+  const double *cache_n = (const double *)lay.cache + ri.cache_off * site_vals;
+  const int2 *bonds_n = lay.bonds + ri.bond_off;
+  const float *jr = lay.jr + ri.site_off, *jd = lay.jd + ri.site_off;
+  const int64_t L2 = int64_t(L) * L;
+  const double beta = lay.beta;
+  double *rs = (double *)lay.samp_scratch + (ri.line_off * int64_t(lay.max_samples) + int64_t(act ? sid : 0) * L) * PCH;
+  uint8_t *st = (FORCED ? nullptr : out_states + int64_t(S) * ri.site_off + int64_t(act ? sid : 0) * L2);
+  const uint8_t *st_in = FORCED ? in_states + int64_t(S) * ri.site_off + int64_t(act ? sid : 0) * L2 : nullptr;
+  auto state_at = [&](int i) -> int { return FORCED ? st_in[i] : st[i]; };
+  double lq = 0.0, E = 0.0;
+  int64_t group = -1;
+  U64x4 words{};
+  bool bad = false;
+  auto stage = [&](const double *A) {
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < site_vals; e += blockDim.x) As[e] = A[e];
+    __syncthreads();
+  };
+  for (int r = 0; r < L; ++r) {
+    const double *row = cache_n + int64_t(r) * L * site_vals;
+    const int2 *bd = bonds_n + int64_t(r) * (L + 1);
+    // right pass: R_{L-1} = 1, R_c = T_{c+1}[s_up] R_{c+1}, normalised, spilled
+    double Rv = lane == 0 ? 1.0 : 0.0;
+    if (act && lane < PCH) rs[int64_t(L - 1) * PCH + lane] = Rv;
+    for (int c = L - 2; c >= 0; --c) {
+      stage(row + int64_t(c + 1) * site_vals);
+      const int Dl = bd[c + 1].x, Dr = bd[c + 2].x;
+      double w[PQ];
+      const int su = (r > 0 && act) ? state_at((r - 1) * L + c + 1) : 0;
+#pragma unroll
+      for (int s = 0; s < PQ; ++s)
+        w[s] = (s < q && r > 0) ? pweight(beta, (double)jd[(r - 1) * L + c + 1], s == su) : (s < q ? 1.0 : 0.0);
+      double acc = 0.0;
+      for (int b = 0; b < Dr; ++b) {
+        const double rb = __shfl_sync(0xffffffffu, Rv, b);
+        if (lane < Dl) {
+          double t = 0.0;
+#pragma unroll
+          for (int s = 0; s < PQ; ++s)
+            if (s < q) t += w[s] * As[(s * chi + lane) * chi + b];
+          acc += t * rb;
+        }
+      }
+      const double nrm = sqrt(pwarp_sum(acc * acc));
+      Rv = nrm > 0.0 ? acc / nrm : 0.0;
+      if (act && lane < PCH) rs[int64_t(c) * PCH + lane] = lane < Dl ? Rv : 0.0;
+    }
+    __syncwarp();
+    // left sweep
+    double lv = lane == 0 ? 1.0 : 0.0;
+    for (int c = 0; c < L; ++c) {
+      stage(row + int64_t(c) * site_vals);
+      const int Dl = bd[c].x, Dr = bd[c + 1].x;
+      const double Rc = (lane < Dr) ? rs[int64_t(c) * PCH + lane] : 0.0;
+      double v[PQ], rho[PQ];
+#pragma unroll
+      for (int s = 0; s < PQ; ++s) v[s] = 0.0;
+      for (int a = 0; a < Dl; ++a) {
+        const double la = __shfl_sync(0xffffffffu, lv, a);
+        if (lane < Dr) {
+#pragma unroll
+          for (int s = 0; s < PQ; ++s)
+            if (s < q) v[s] += la * As[(s * chi + a) * chi + lane];
+        }
+      }
+      const int i = r * L + c;
+      const int su = (r > 0 && act) ? state_at((r - 1) * L + c) : 0;
+      double tot = 0.0;
+#pragma unroll
+      for (int s = 0; s < PQ; ++s) {
+        rho[s] = 0.0;
+        if (s < q) {
+          rho[s] = fabs(pwarp_sum(v[s] * Rc));
+          if (r > 0) rho[s] *= pweight(beta, (double)jd[(r - 1) * L + c], s == su);
+          tot += rho[s];
+        }
+      }
+      int k;
+      if (FORCED) {
+        k = act ? st_in[i] : 0;
+      } else {
+        if ((i >> 2) != group) {
+          group = i >> 2;
+          words = philox4x64_10((uint64_t)group, prop_base + (uint64_t)(act ? sid : 0), (uint64_t)ri.gid,
+                                 TAG_SPIN, seed, 0ull);
+        }
+        const double u = word_to_uniform(words.x[i & 3]);
+        k = q - 1;
+        double cum = 0.0;
+        bool found = false;
+#pragma unroll
+        for (int s = 0; s < PQ - 1; ++s) {
+          if (s < q - 1 && !found) {
+            cum += rho[s] / tot;
+            if (u < cum) { k = s; found = true; }
+          }
+        }
+      }
+      if (!(tot > 0.0) || !isfinite(tot)) bad = true;
+      double rk = rho[0];
+#pragma unroll
+      for (int s = 1; s < PQ; ++s) rk = (s == k) ? rho[s] : rk;
+      lq += log(rk / tot);
+      if (c > 0) E -= (double)jr[r * L + c - 1] * (k == state_at(i - 1) ? 1.0 : 0.0);
+      if (r > 0) E -= (double)jd[(r - 1) * L + c] * (k == su ? 1.0 : 0.0);
+      if (!FORCED && act && lane == 0) st[i] = (uint8_t)k;
+      __syncwarp();
+      double vk = v[0];
+#pragma unroll
+      for (int s = 1; s < PQ; ++s) vk = (s == k) ? v[s] : vk;
+      const double nrm = sqrt(pwarp_sum(vk * vk));
+      lv = nrm > 0.0 ? vk / nrm : 0.0;
+    }
+  }
+  if (act && lane == 0) {
+    out_logq[int64_t(n) * S + sid] = lq;
+    out_E[int64_t(n) * S + sid] = E;
+    if (bad) set_flag(lay.flags, n, FLAG_NUMERIC);
+  }
+}
+
+}  // namespace
+
+int64_t potts_slot_bytes(int L_max) {
+  return align256(int64_t(L_max) * PM * PD * 8) + align256(int64_t(L_max) * 8);
+}
+
+// q and chi limits of the float64 Potts kernels (panel sizes in shared memory)
+bool potts_supported(int q, int chi) { return q >= 3 && q <= PQ && chi <= PCH && q * q * chi <= PM; }
+
+int potts_scratch_ch() { return PCH; }
+
+cudaError_t launch_potts_build(const Layout &lay, int q, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(potts_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       PottsSmem::bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(lay.counter, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  potts_build_kernel<<<lay.env_slots, PT, PottsSmem::bytes, st>>>(lay, q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_potts_log_z(const Layout &lay, int q, double *logz, cudaStream_t st) {
+  potts_log_z_kernel<<<lay.n_real, 32, 0, st>>>(lay, q, logz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_potts_sample(const Layout &lay, int q, int S, uint64_t seed, uint64_t base,
+                                const uint8_t *in, uint8_t *out, double *lq, double *E, cudaStream_t st) {
+  const int bpr = (S + PS_CHAINS - 1) / PS_CHAINS;
+  const size_t smem = size_t(q) * lay.chi * lay.chi * 8;
+  if (in) potts_sample_kernel<true><<<lay.n_real * bpr, 32 * PS_CHAINS, smem, st>>>(lay, q, S, seed, base, in, out, lq, E);
+  else potts_sample_kernel<false><<<lay.n_real * bpr, 32 * PS_CHAINS, smem, st>>>(lay, q, S, seed, base, in, out, lq, E);
+  return cudaGetLastError();
+}
+
+}  // namespace tnmc
