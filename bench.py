@@ -184,16 +184,22 @@ def oracle_sample(wl, seconds: float = 15.0):
 
 
 def _oracle_realization(wl, n, seconds):
-    from oracle import bmps
+    from oracle import bmps, potts
     L, chi, beta = wl.Ls[n], wl.chi, wl.beta
     Jh, Jv = wl.realization(n)
     t0 = time.perf_counter()
-    mps, lam = bmps.bottom_row_mps(Jh[L - 1], beta)
+    if wl.q > 2:
+        bottom = lambda Jh_row: potts.bottom_row_mps(Jh_row, beta, wl.q)
+        row_mpo = lambda Jh_row, Jv_row: potts.row_mpo(Jh_row, Jv_row, beta, wl.q)
+    else:
+        bottom = lambda Jh_row: bmps.bottom_row_mps(Jh_row, beta)
+        row_mpo = lambda Jh_row, Jv_row: bmps.row_mpo(Jh_row, Jv_row, beta)
+    mps, lam = bottom(Jh[L - 1])
     times, dims = [], []
     for r in range(L - 1, -1, -1):
         ts = time.perf_counter()
         if r < L - 1:
-            mpo, sc = bmps.row_mpo(Jh[r], Jv[r], beta)
+            mpo, sc = row_mpo(Jh[r], Jv[r])
             mps = bmps.multiply(mpo, mps)
         mps = bmps.compress(mps, chi)[0]
         times.append(time.perf_counter() - ts)
@@ -393,7 +399,7 @@ def run_ours(args, wl):
     from workloads import Workload
     n_all = world * wl.n_real
     gw = Workload(wl.name, [wl.Ls[g % wl.n_real] for g in range(n_all)], wl.beta, wl.chi, wl.S,
-                  kind=wl.kind, base_seed=wl.base_seed, p=wl.p)
+                  kind=wl.kind, base_seed=wl.base_seed, p=wl.p, q=wl.q)
     ids = shard.lpt_partition(gw.Ls, gw.chi, world)[rank]
     my_Ls = [gw.Ls[g] for g in ids]
     peaks_alu = measure_alu_peaks(dev)
@@ -402,12 +408,13 @@ def run_ours(args, wl):
     S = wl.S
     ckpt = args.ckpt if args.ckpt >= 0 else (32 if max(wl.Ls) >= 1024 else 0)
     t = P.TNMC(my_Ls, wl.chi, wl.beta, args.prec, max_samples=S, device=dev, cutoff=args.cutoff,
-               ckpt_every=ckpt)
+               ckpt_every=ckpt, q=wl.q)
     t.set_realization_ids(ids)
     n_mine = len(ids)
     # the build layout: the autotuner times the candidates on the bottom rows of these
     # realizations (setup, outside the timed region)
-    tune = t.autotune(J, rows=args.tune_rows) if args.tune_rows > 0 else {}
+    # (the Potts build has one layout: nothing to tune)
+    tune = t.autotune(J, rows=args.tune_rows) if args.tune_rows > 0 and wl.q == 2 else {}
     stream = t.stream
     learned = None
     if args.learned:
@@ -567,7 +574,9 @@ def run_ours(args, wl):
         # pass per realization (2 D^2 values, shared by the S chains) and the spin written
         esz = 4 if args.prec in ("fp32", "tf32", "bf16") else 8
         samp_sites = S * site_rows
-        samp_bytes = samp_sites * (2.0 * dmean * esz + 2.0 * dmean * dmean * esz / S + 1.0)
+        # (a Potts site is q dense D x D matrices, an Ising site one parity-form matrix)
+        site_mats = wl.q if wl.q > 2 else 1
+        samp_bytes = samp_sites * (2.0 * dmean * esz + 2.0 * site_mats * dmean * dmean * esz / S + 1.0)
         hbm_peak = peaks.get("hbm_gbs") or 6484.6
         cpu = None
         if world == 1 and args.cpu_baseline:
@@ -588,9 +597,11 @@ def run_ours(args, wl):
                       "bf16": "f32 (tensor-core products from bf16 operands)",
                       "dfloat": "f32x2 (double-float)"}[args.prec],
             "data": ("synthetic Gaussian N(0,1) disorder, seeded" if wl.kind == "gauss"
-                     else "synthetic +-J disorder (p = 1/2), seeded"),
+                     else "synthetic +-J disorder (p = 1/2), seeded")
+                    + (f", {wl.q}-state Potts" if wl.q > 2 else ""),
             "config": {"workload": wl.name, "L": wl.Ls[0], "chi": wl.chi, "beta": wl.beta,
                        "realizations_per_gpu": wl.n_real, "realizations": n_all, "samples_per_realization": S,
+                       "q_states": wl.q,
                        "precision": args.prec, "cutoff": cutoff_primary, "ckpt_every": ckpt,
                        "build_variant": variant_primary, "autotune_ms": tune,
                        "learned_correction": bool(args.learned),

@@ -241,7 +241,11 @@ tnmc_status tnmc_mh_step(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
  *            setup (in float64 including the QR that preconditions the
  *            Jacobi), Jacobi, selection + stores, and the row's algorithmic
  *            flops: textbook counts of its QRs (2mn^2 - 2n^3/3, twice for Q),
- *            SVDs (4a^2b + 8ab^2 + 9b^3, Golub-Reinsch) and products). */
+ *            SVDs (4a^2b + 8ab^2 + 9b^3, Golub-Reinsch) and products).
+ *            Potts handles (q_states >= 3) accept d_rowinfo only and fill its
+ *            mean bond, SVD, sweep and flop fields and, in the four cycle fields,
+ *            phase A, the Theta products, the Jacobi sweeps and selection + stores
+ *            (the others 0); d_logits and d_spectra return TNMC_ERR_UNSUPPORTED. */
 tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spectra,
                                  double *d_rowinfo);
 

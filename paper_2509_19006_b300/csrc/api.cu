@@ -319,7 +319,7 @@ void tnmc_destroy(tnmc_handle *h) { delete h; }
 tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spectra,
                                  double *d_rowinfo) {
   if (!h) return TNMC_ERR_ARG;
-  if (h->q > 2 && (d_logits || d_spectra || d_rowinfo)) return TNMC_ERR_UNSUPPORTED;
+  if (h->q > 2 && (d_logits || d_spectra)) return TNMC_ERR_UNSUPPORTED;   // Potts: row records only
   h->lay.dbg_logits = d_logits;
   h->lay.dbg_spectra = d_spectra;
   h->lay.dbg_rowinfo = d_rowinfo;

@@ -14,9 +14,10 @@
 //   phase A (sites 0 -> L-1): C[s] = sum_n Bv[s, n] A_c[n] of the row below, the carried
 //     triangular factor absorbed, T[(k, s), (b, b')] = Bh[s, b] sum_a' R[k, (s, a')] C[s][a', b'],
 //     a Householder QR of T, R normalised (its norm into lambda_r), Q kept for phase B;
-//   phase B (sites L-1 -> 0): Theta = Q_c (US) as (left bond) x (q x right bond), a one-sided
-//     Jacobi SVD on the rows of [Theta | I] (the identity block accumulates U^T), the chi
-//     largest singular values above cutoff x largest kept, V^T stored, U S / s_max carried.
+//   phase B (sites L-1 -> 0): Theta = Q_c (US) as (left bond) x (q x right bond), a pivoted
+//     Householder QR of Theta, a one-sided Jacobi SVD on the rows of [R | Q^T] (the Q^T block
+//     ends as U^T), the chi largest singular values above cutoff x largest kept, V^T stored,
+//     U S / s_max carried.
 // The bottom row is the same sweep over a trivial row below (C = 1).
 //
 // potts_sample_kernel: one warp per chain, eight chains per CTA sharing the staged site
@@ -128,13 +129,113 @@ __device__ void p_form_q(double *A, const double *tau, int m, int kq) {
   }
 }
 
+// Householder QR with column pivoting (Businger & Golub, 1965) of the row-major m x n
+// matrix A (element (i, j) at A[i * PLDT + j]) by the whole CTA: at step j the remaining
+// column of largest norm below row j (ties: lower index) is swapped into place; R ends in
+// the upper triangle, the reflectors below it, piv[k] = the original index of column k.
+// The column norms below the current row are recomputed exactly in every update pass.
+__device__ void p_qr_pivot_rows(double *A, int m, int n, double *tau, double *cn, int *piv) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int kq = min(m, n);
+  for (int k = warp; k < n; k += PT / 32) {
+    double s2 = 0.0;
+    for (int i = lane; i < m; i += 32) s2 += A[i * PLDT + k] * A[i * PLDT + k];
+    s2 = pwarp_sum(s2);
+    if (lane == 0) { cn[k] = s2; piv[k] = k; }
+  }
+  __syncthreads();
+  for (int j = 0; j < kq; ++j) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bk = j;
+      for (int k = j + lane; k < n; k += 32)
+        if (cn[k] > best) { best = cn[k]; bk = k; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        if (ob > best || (ob == best && ok < bk)) { best = ob; bk = ok; }
+      }
+      if (bk != j) {
+        for (int i = lane; i < m; i += 32) {
+          const double x = A[i * PLDT + j];
+          A[i * PLDT + j] = A[i * PLDT + bk];
+          A[i * PLDT + bk] = x;
+        }
+        if (lane == 0) {
+          const double c = cn[j]; cn[j] = cn[bk]; cn[bk] = c;
+          const int p = piv[j]; piv[j] = piv[bk]; piv[bk] = p;
+        }
+      }
+      __syncwarp();
+      double s2 = 0.0;
+      for (int i = j + 1 + lane; i < m; i += 32) s2 += A[i * PLDT + j] * A[i * PLDT + j];
+      s2 = pwarp_sum(s2);
+      const double x0 = A[j * PLDT + j];
+      if (s2 == 0.0) {
+        if (lane == 0) tau[j] = 0.0;
+      } else {
+        const double mu = sqrt(x0 * x0 + s2);
+        const double be = x0 <= 0.0 ? mu : -mu;
+        const double sc = 1.0 / (x0 - be);
+        for (int i = j + 1 + lane; i < m; i += 32) A[i * PLDT + j] *= sc;
+        if (lane == 0) { tau[j] = (be - x0) / be; A[j * PLDT + j] = be; }
+      }
+    }
+    __syncthreads();
+    const double tj = tau[j];
+    for (int k = j + 1 + warp; k < n; k += PT / 32) {
+      double w = lane == 0 ? A[j * PLDT + k] : 0.0;
+      for (int i = j + 1 + lane; i < m; i += 32) w += A[i * PLDT + j] * A[i * PLDT + k];
+      w = pwarp_sum(w) * tj;
+      if (lane == 0) A[j * PLDT + k] -= w;
+      double nn = 0.0;
+      for (int i = j + 1 + lane; i < m; i += 32) {
+        const double x = A[i * PLDT + k] - w * A[i * PLDT + j];
+        A[i * PLDT + k] = x;
+        nn += x * x;
+      }
+      nn = pwarp_sum(nn);
+      if (lane == 0) cn[k] = nn;
+    }
+    __syncthreads();
+  }
+}
+
+// Rotation of one Jacobi pair (alpha = |a|^2, beta = |b|^2, gamma = a . b): the tangent t of
+// the angle that makes the rows orthogonal, computed in float32 after an exact
+// power-of-two rescale (B300's float64 divide and square root take ~700 cycles each),
+// then c = 1 / sqrt(1 + t^2) by two Newton steps from the float32 reciprocal square root,
+// so that c^2 (1 + t^2) = 1 to float64 rounding: (c, s = c t) is an exact rotation whose
+// angle is the Jacobi angle to ~1e-7; the residual inner product is left to the next sweep.
+__device__ __forceinline__ void p_rotation(double al, double be, double ga, double &t, double &cs,
+                                           double &sn) {
+  const long long bits = __double_as_longlong(fmax(al, be));
+  const int e = int((bits >> 52) & 0x7ff) - 1023;
+  const double sc = __longlong_as_double((long long)(1023 - e) << 52);   // 2^-e, exact
+  const float d = float((be - al) * sc), g2 = 2.f * float(ga * sc);
+  const float zf = d / g2;
+  float tf;
+  if (fabsf(zf) > 1e18f) tf = 0.5f / zf;
+  else tf = (zf >= 0.f ? 1.f : -1.f) / (fabsf(zf) + sqrtf(1.f + zf * zf));
+  t = double(tf);
+  const double x = 1.0 + t * t;
+  double y = double(rsqrtf(float(x)));
+  y = y * (1.5 - 0.5 * x * y * y);
+  y = y * (1.5 - 0.5 * x * y * y);
+  cs = y;
+  sn = y * t;
+}
+
 // One-sided Jacobi on the nr rows of B (ld PLDT): inner products over the first nc
 // columns, rotations over nc + nu columns. Round-robin (circle) schedule, 16 lanes per
-// row pair, the three inner products measured exactly in every round. A pair is rotated
-// while |gamma| > tol sqrt(alpha beta), tol = 8 sqrt(nc) eps, unless either row is below
-// eps x the largest row (rounding noise). Returns the sweeps taken.
-__device__ int p_jacobi(double *B, int nr, int nc, int nu, int *sh_flag) {
-  const int tid = threadIdx.x;
+// row pair. The squared row norms are measured exactly at the start of every sweep and
+// updated within it (alpha - t gamma, beta + t gamma), so a round computes one inner
+// product per pair. A pair is rotated while |gamma| > tol sqrt(alpha beta), tol = 8
+// sqrt(nc) eps, unless either row is below eps x the largest row (rounding noise).
+// Returns the sweeps taken.
+__device__ int p_jacobi(double *B, int nr, int nc, int nu, int *sh_flag, double *nrm2) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (nr <= 1) return 0;
   constexpr int TPP = 16;
   const int P = nr + (nr & 1), np = P / 2;
@@ -142,21 +243,24 @@ __device__ int p_jacobi(double *B, int nr, int nc, int nu, int *sh_flag) {
   const double eps = 1.1102230246251565e-16;
   const double tol2 = 64.0 * eps * eps * double(nc > 4 ? nc : 4);
   __shared__ double sh_mx;
-  if (tid == 0) {
-    double mx = 0.0;
-    for (int i = 0; i < nr; ++i) {
-      double s = 0.0;
-      for (int x = 0; x < nc; ++x) s += B[i * PLDT + x] * B[i * PLDT + x];
-      mx = fmax(mx, s);
-    }
-    sh_mx = mx;
-  }
-  __syncthreads();
-  const double floor2 = sh_mx * eps * eps;
   int sweep = 0;
   for (; sweep < P_MAX_SWEEPS; ++sweep) {
+    // exact squared norms, one warp per row
+    for (int i = warp; i < nr; i += PT / 32) {
+      double s2 = 0.0;
+      for (int x = lane; x < nc; x += 32) s2 += B[i * PLDT + x] * B[i * PLDT + x];
+      s2 = pwarp_sum(s2);
+      if (lane == 0) nrm2[i] = s2;
+    }
     if (tid == 0) *sh_flag = 0;
     __syncthreads();
+    if (tid == 0 && sweep == 0) {
+      double mx = 0.0;
+      for (int i = 0; i < nr; ++i) mx = fmax(mx, nrm2[i]);
+      sh_mx = mx;
+    }
+    __syncthreads();
+    const double floor2 = sh_mx * eps * eps;
     for (int k = 0; k < P - 1; ++k) {
       int i = -1, j = -1;
       if (g < np) {
@@ -165,30 +269,27 @@ __device__ int p_jacobi(double *B, int nr, int nc, int nu, int *sh_flag) {
         j = 1 + (p1 - 1 + k) % (P - 1);
         if (i >= nr || j >= nr) i = j = -1;
       }
-      double al = 0.0, be = 0.0, ga = 0.0;
+      double ga = 0.0;
       if (i >= 0) {
         const double *a = B + i * PLDT, *b = B + j * PLDT;
-        for (int x = gl; x < nc; x += TPP) {
-          al += a[x] * a[x]; be += b[x] * b[x]; ga += a[x] * b[x];
-        }
+        for (int x = gl; x < nc; x += TPP) ga += a[x] * b[x];
       }
 #pragma unroll
-      for (int o = TPP / 2; o > 0; o >>= 1) {
-        al += __shfl_xor_sync(0xffffffffu, al, o);
-        be += __shfl_xor_sync(0xffffffffu, be, o);
-        ga += __shfl_xor_sync(0xffffffffu, ga, o);
-      }
-      if (i >= 0 && al > floor2 && be > floor2 && ga * ga > tol2 * al * be) {
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-        double *a = B + i * PLDT, *b = B + j * PLDT;
-        for (int x = gl; x < nc + nu; x += TPP) {
-          const double av = a[x], bv = b[x];
-          a[x] = cs * av - sn * bv;
-          b[x] = sn * av + cs * bv;
+      for (int o = TPP / 2; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+      if (i >= 0) {
+        const double al = nrm2[i], be = nrm2[j];
+        if (al > floor2 && be > floor2 && ga * ga > tol2 * al * be) {
+          double t, cs, sn;
+          p_rotation(al, be, ga, t, cs, sn);
+          double *a = B + i * PLDT, *b = B + j * PLDT;
+          for (int x = gl; x < nc + nu; x += TPP) {
+            const double av = a[x], bv = b[x];
+            a[x] = cs * av - sn * bv;
+            b[x] = sn * av + cs * bv;
+          }
+          __syncwarp(0xffffu << (tid & 16));   // the pair's 16 lanes have read the norms
+          if (gl == 0) { nrm2[i] = al - t * ga; nrm2[j] = be + t * ga; *sh_flag = 1; }
         }
-        if (gl == 0) *sh_flag = 1;
       }
       __syncthreads();
     }
@@ -206,8 +307,13 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
   double *Th = W + PottsSmem::oT, *US = W + PottsSmem::oU, *tau = W + PottsSmem::oTau;
   double *sn = W + PottsSmem::oSn;
   __shared__ double sh_red[PT / 32];
-  __shared__ double sh_lam, sh_smax;
-  __shared__ int sh_n, sh_flag, sh_keep, sh_kprev;
+  __shared__ double sh_nrm2[PD];   // Jacobi row norms
+  __shared__ double sh_cn[PD];     // column norms of the pivoted QR
+  __shared__ int sh_piv[PD], sh_ipiv[PD];
+  __shared__ double sh_lam, sh_smax, sh_flops, sh_dsum;
+  __shared__ int sh_n, sh_flag, sh_keep, sh_kprev, sh_sweeps, sh_svds;
+  __shared__ long long sh_clk[4];   // cycles of the row: phase A, Theta products, Jacobi, selection + stores
+  long long t_mark = 0;
   __shared__ int sh_src[PD];
   __shared__ double sh_Bh[PQ * PQ], sh_Bv[PQ * PQ];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -254,6 +360,9 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           sh_lam += s;
           sh_kprev = 1;
           Rb[0] = 1.0;
+          sh_flops = 0.0; sh_dsum = 0.0; sh_sweeps = 0; sh_svds = 0;
+          for (int f = 0; f < 4; ++f) sh_clk[f] = 0;
+          t_mark = clock64();
         }
         __syncthreads();
       }
@@ -332,9 +441,16 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           const int col = e / m, i = e % m;
           qs[i + col * PM] = Ap[i + col * PM];
         }
-        if (tid == 0) { info[c] = make_int2(kprev, kq); sh_kprev = kq; }
+        if (tid == 0) {
+          info[c] = make_int2(kprev, kq);
+          sh_kprev = kq;
+          // textbook flops: the MPO x MPS product, Householder QR with explicit Q
+          const double mm = m, nn = ncol, kk = kq;
+          sh_flops += 2.0 * mm * nn * (c == 0 ? 1.0 : Dl) + 2.0 * (2.0 * mm * nn * kk - 2.0 * kk * kk * kk / 3.0);
+        }
         __syncthreads();
       }
+      if (tid == 0) { const long long t1 = clock64(); sh_clk[0] += t1 - t_mark; t_mark = t1; }
       // ===================== phase B: truncating SVD sweep, right to left
       int kr = 1;   // kept bond to the right of the current site
       for (int c = L - 1; c >= 0; --c) {
@@ -357,6 +473,7 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           }
         }
         __syncthreads();
+        if (tid == 0) { const long long t1 = clock64(); sh_clk[1] += t1 - t_mark; t_mark = t1; }
         double *site_dst = dst_row + int64_t(c) * site_vals;
         if (c == 0) {
           // site 0 (left bond 1): divided by its norm
@@ -381,19 +498,43 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
             bonds_n[int64_t(r) * (L + 1) + L] = make_int2(1, 0);
             if (L > 1) bonds_n[int64_t(r) * (L + 1) + 1] = make_int2(kr, 0);
             lay.lam[ri.row_off + r] = sh_lam;
+            if (lay.dbg_rowinfo) {   // the Ising build's row record: bond, sweeps and flops fields
+              double *ro = lay.dbg_rowinfo + (ri.row_off + r) * 14;
+              for (int f = 0; f < 14; ++f) ro[f] = 0.0;
+              ro[5] = L > 1 ? sh_dsum / (L - 1) : 1.0;
+              ro[6] = sh_svds;
+              ro[7] = sh_svds > 0 ? double(sh_sweeps) / sh_svds : 0.0;
+              for (int f = 0; f < 4; ++f) ro[8 + f] = double(sh_clk[f]);
+              ro[13] = sh_flops;
+            }
           }
           __syncthreads();
           break;
         }
-        // [Theta | I]: the rotations accumulate U^T in the identity block
-        for (int e = tid; e < Dl * Dl; e += PT) {
+        // QR preconditioning: Theta P = Q R (pivoted Householder), then the sweeps rotate the
+        // rr = min(Dl, nc) rows of [R | Q^T], which end as S V^T P and U^T; one-sided Jacobi on
+        // the graded triangular factor needs far fewer sweeps than on [Theta | I]
+        // (Drmac & Veselic, SIAM J. Matrix Anal. Appl. 29, 2008). P is undone at the store.
+        const int rr = min(Dl, nc);
+        p_qr_pivot_rows(Th, Dl, nc, tau, sh_cn, sh_piv);
+        for (int e = tid; e < Dl * rr; e += PT) {   // reflectors to Ap (column-major), R kept
+          const int i = e / rr, j = e % rr;
+          double v = 0.0;
+          if (i > j) { v = Th[i * PLDT + j]; Th[i * PLDT + j] = 0.0; }
+          Ap[i + j * PM] = v;
+        }
+        for (int b = tid; b < nc; b += PT) sh_ipiv[sh_piv[b]] = b;
+        __syncthreads();
+        p_form_q(Ap, tau, Dl, rr);
+        for (int e = tid; e < rr * Dl; e += PT) {
           const int i = e / Dl, p = e % Dl;
-          Th[i * PLDT + nc + p] = (i == p) ? 1.0 : 0.0;
+          Th[i * PLDT + nc + p] = Ap[p + i * PM];
         }
         __syncthreads();
-        p_jacobi(Th, Dl, nc, Dl, &sh_flag);
+        const int nsw = p_jacobi(Th, rr, nc, Dl, &sh_flag, sh_nrm2);
+        if (tid == 0) { const long long t1 = clock64(); sh_clk[2] += t1 - t_mark; t_mark = t1; }
         // singular values = row norms; keep the chi largest above cutoff x largest
-        for (int i = tid; i < Dl; i += PT) {
+        for (int i = tid; i < rr; i += PT) {
           double s2 = 0.0;
           for (int x = 0; x < nc; ++x) s2 += Th[i * PLDT + x] * Th[i * PLDT + x];
           sn[i] = sqrt(s2);
@@ -401,26 +542,32 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
         __syncthreads();
         if (tid == 0) {
           double mx = 0.0;
-          for (int i = 0; i < Dl; ++i) mx = fmax(mx, sn[i]);
+          for (int i = 0; i < rr; ++i) mx = fmax(mx, sn[i]);
           sh_smax = mx;
         }
         __syncthreads();
         const double smax = sh_smax, thr = smax * lay.cutoff;
-        if (tid < Dl) {
+        if (tid < rr) {
           const int i = tid;
           int rank = 0;
-          for (int j = 0; j < Dl; ++j) rank += (sn[j] > sn[i]) || (sn[j] == sn[i] && j < i);
+          for (int j = 0; j < rr; ++j) rank += (sn[j] > sn[i]) || (sn[j] == sn[i] && j < i);
           const bool keep = rank < chi && (sn[i] > thr || rank == 0);
           if (keep) sh_src[rank] = i;
         }
         if (tid == 0) {
           int kk = 0;
-          for (int i = 0; i < Dl; ++i) {
+          for (int i = 0; i < rr; ++i) {
             int rank = 0;
-            for (int j = 0; j < Dl; ++j) rank += (sn[j] > sn[i]) || (sn[j] == sn[i] && j < i);
+            for (int j = 0; j < rr; ++j) rank += (sn[j] > sn[i]) || (sn[j] == sn[i] && j < i);
             kk += (rank < chi && (sn[i] > thr || rank == 0)) ? 1 : 0;
           }
           sh_keep = kk;
+          sh_dsum += kk;
+          if (nsw > 0) { sh_sweeps += nsw; sh_svds += 1; }
+          // textbook flops: the Theta product and a Golub-Reinsch SVD of the Dl x nc matrix
+          const double a = Dl > nc ? Dl : nc, b = Dl > nc ? nc : Dl;
+          sh_flops += 4.0 * a * a * b + 8.0 * a * b * b + 9.0 * b * b * b;
+          if (c < L - 1) sh_flops += 2.0 * Dl * q * double(info[c].y) * kr;
           if (smax > 0.0 && isfinite(smax)) sh_lam += log(smax);
           else set_flag(lay.flags, n, FLAG_NUMERIC);
         }
@@ -432,7 +579,7 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           double v = 0.0;
           if (a < kk && b < kr) {
             const int i = sh_src[a];
-            v = Th[i * PLDT + s * kr + b] / sn[i];
+            v = Th[i * PLDT + sh_ipiv[s * kr + b]] / sn[i];   // column (s, b) sits at ipiv
           }
           site_dst[e] = v;
         }
@@ -446,6 +593,7 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
         if (tid == 0) bonds_n[int64_t(r) * (L + 1) + c] = make_int2(kk, 0);
         kr = kk;
         __syncthreads();
+        if (tid == 0) { const long long t1 = clock64(); sh_clk[3] += t1 - t_mark; t_mark = t1; }
       }
     }
   }

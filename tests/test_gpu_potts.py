@@ -136,3 +136,21 @@ def test_potts_argument_and_mode_errors(P):
     with pytest.raises(P.TnmcError) as e:
         t.mh_init(1)                                          # random starts draw Ising bits
     assert e.value.status == 7
+
+
+def test_potts_row_records_match_the_oracle_bonds(P):
+    Ls, q, chi, beta = [10, 6, 8], 3, 16, 0.7
+    reals = parity.realizations(Ls, "pmj")
+    t = P.TNMC(Ls, chi, beta, "fp64", max_samples=8, q=q, cutoff=1e-6)
+    _, _, ri = t.set_diagnostics(rowinfo=True)
+    t.build_envs(torch.from_numpy(parity.packed_J(reals)).cuda())
+    torch.cuda.synchronize()
+    rec = ri.cpu().numpy().reshape(-1, 14)
+    off = 0
+    for (Jh, Jv), L in zip(reals, Ls):
+        rows = potts.build_envs(Jh, Jv, beta, q, chi, 1e-6)
+        for r in range(L):
+            mean_bond = np.mean([A.shape[0] for A in rows[r].tensors[1:]])
+            assert rec[off + r, 5] == mean_bond, (L, r)
+            assert rec[off + r, 13] > 0 and rec[off + r, 7] >= 1
+        off += L

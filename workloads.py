@@ -71,6 +71,7 @@ class Workload:
     kind: str = "pmj"
     base_seed: int = 1000
     p: float = 0.5            # antiferromagnetic bond probability of the +-J model
+    q: int = 2                # 2: Ising; 3 or 4: the q-state Potts extension
 
     @property
     def n_real(self) -> int:
@@ -104,6 +105,8 @@ def config(name: str) -> Workload:
         return Workload("paper_L1024_chi8_beta1_n64_S256", [1024] * 64, 1.0, 8, 256)
     if name == "L128b1x8":   # 8 realizations at L=128, beta=1, chi=32 (captures of the TF32 / BF16 builds)
         return Workload("L128_chi32_beta1_n8_S64", [128] * 8, 1.0, 32, 64)
+    if name == "potts":      # the q-state Potts extension: 64 +-J realizations, q = 3, L=64, beta=1, chi=16
+        return Workload("potts3_L64_chi16_beta1_n64_S256", [64] * 64, 1.0, 16, 256, q=3)
     # small cases of the L=256 workload's kernels (same beta, chi), for profiler captures
     if name == "L128x8":
         return Workload("L128_chi64_beta3_n8_S256", [128] * 8, 3.0, 64, 256)
