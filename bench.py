@@ -830,7 +830,7 @@ def run_env_once(args, wl):
     import torch
     import paper_2509_19006_b300 as P
     J = torch.from_numpy(wl.packed_J()).cuda()
-    t = P.TNMC(wl.Ls, wl.chi, wl.beta, args.prec, max_samples=wl.S, cutoff=args.cutoff)
+    t = P.TNMC(wl.Ls, wl.chi, wl.beta, args.prec, max_samples=wl.S, cutoff=args.cutoff, q=wl.q)
     t.build_envs(J)
     lz = t.log_z()
     torch.cuda.synchronize()

@@ -107,6 +107,8 @@ def config(name: str) -> Workload:
         return Workload("L128_chi32_beta1_n8_S64", [128] * 8, 1.0, 32, 64)
     if name == "potts":      # the q-state Potts extension: 64 +-J realizations, q = 3, L=64, beta=1, chi=16
         return Workload("potts3_L64_chi16_beta1_n64_S256", [64] * 64, 1.0, 16, 256, q=3)
+    if name == "potts_x4":   # 4 realizations of the Potts workload (profiler captures)
+        return Workload("potts3_L64_chi16_beta1_n4_S64", [64] * 4, 1.0, 16, 64, q=3)
     # small cases of the L=256 workload's kernels (same beta, chi), for profiler captures
     if name == "L128x8":
         return Workload("L128_chi64_beta3_n8_S256", [128] * 8, 3.0, 64, 256)
