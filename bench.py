@@ -413,8 +413,12 @@ def run_ours(args, wl):
     n_mine = len(ids)
     # the build layout: the autotuner times the candidates on the bottom rows of these
     # realizations (setup, outside the timed region)
-    # (the Potts build has one layout: nothing to tune)
-    tune = t.autotune(J, rows=args.tune_rows) if args.tune_rows > 0 and wl.q == 2 else {}
+    # (the Potts build has one layout: nothing to tune). A full build first, so the autotuner
+    # times rows from the middle of the lattice, whose bonds are those of the whole build
+    tune = {}
+    if args.tune_rows > 0 and wl.q == 2:
+        t.build_envs(J)
+        tune = t.autotune(J, rows=args.tune_rows)
     stream = t.stream
     learned = None
     if args.learned:

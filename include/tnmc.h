@@ -389,7 +389,11 @@ tnmc_status tnmc_set_realization_ids(tnmc_handle *h, const int64_t *h_ids);
  *   bit 3 (8): in the one-CTA build, 8 lanes per row pair instead of 4;
  *   bit 4 (16): the float32 build (TNMC_FP32, TF32, BF16) on pairs of CTAs where they
  *     fit, its Jacobi chosen by bits 0-1 (0 = 16 lanes on the whole CTA); without it the
- *     float32 build runs one CTA per realization.
+ *     float32 build runs one CTA per realization;
+ *   bit 5 (32): the float32 build's Jacobi preconditioned by a pivoted Householder QR, as
+ *     the float64 and double-float builds always are: fewer sweeps, but the float32 Q is
+ *     orthogonal only to float32 rounding, so the truncation is a little less accurate
+ *     (float64 and double-float ignore the bit).
  * Applies to later tnmc_build_envs calls (and the segment rebuilds of checkpointed
  * handles). Errors: TNMC_ERR_ARG. */
 tnmc_status tnmc_set_build_variant(tnmc_handle *h, int32_t variant);
@@ -399,12 +403,16 @@ int32_t tnmc_get_build_variant(const tnmc_handle *h);
 
 /* Autotuner of the build layout (the paper has no counterpart): ingests d_J (as
  * tnmc_build_envs), then for each candidate layout of the handle's precision builds
- * only the bottom `rows` rows of every realization, timed with CUDA events on the
- * handle's stream, and keeps the fastest for later builds. h_variants / h_ms (host,
- * optional, capacity *h_count on entry) receive the candidates and their times in ms;
- * *h_count receives the number of candidates. Synchronises the stream. The timing
- * launches overwrite bottom rows of the cache, so the handle must be built again
- * (tnmc_build_envs) before proposals. Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+ * `rows` rows of every realization, timed with CUDA events on the handle's stream, and
+ * keeps the fastest for later builds. On a handle that has been built (and holds every
+ * row: no checkpoints, not TNMC_MIXED) the timed rows are the `rows` rows below the
+ * middle of the smallest lattice, rebuilt from the cached row under them, whose bond
+ * dimensions are those of the whole build; otherwise the bottom `rows` rows, whose bonds
+ * are smaller. h_variants / h_ms (host, optional, capacity *h_count on entry) receive the
+ * candidates and their times in ms; *h_count receives the number of candidates.
+ * Synchronises the stream. The timing launches overwrite rows of the cache, so the
+ * handle must be built again (tnmc_build_envs) before proposals.
+ * Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA, TNMC_ERR_UNSUPPORTED (Potts handles). */
 tnmc_status tnmc_autotune_build(tnmc_handle *h, const float *d_J, int32_t rows, int32_t *h_variants,
                                 float *h_ms, int32_t *h_count);
 

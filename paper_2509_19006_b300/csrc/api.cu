@@ -366,7 +366,7 @@ tnmc_status tnmc_set_realization_ids(tnmc_handle *h, const int64_t *h_ids) {
 }
 
 tnmc_status tnmc_set_build_variant(tnmc_handle *h, int32_t variant) {
-  if (!h || variant < 0 || variant > 31 || (variant & 3) == 3) return TNMC_ERR_ARG;
+  if (!h || variant < 0 || variant > 63 || (variant & 3) == 3) return TNMC_ERR_ARG;
   h->lay.variant = variant;
   return TNMC_OK;
 }
@@ -380,8 +380,15 @@ tnmc_status tnmc_autotune_build(tnmc_handle *h, const float *d_J, int32_t rows, 
   // candidate layouts of this precision (env_build.cu, VARIANT_*)
   std::vector<int32_t> cand;
   if (h->env_code == 0 || h->env_code == 3) cand = {0, 1, 2, 4, 4 | 8};
-  else if (h->env_code == 1) cand = {0, 8, 16, 16 | 1, 16 | 2};   // one CTA, or pairs (bit 4)
+  else if (h->env_code == 1)   // one CTA, or pairs (bit 4); with or without the QR preconditioning (bit 5)
+    cand = {0, 8, 16, 16 | 1, 16 | 2, 32, 32 | 8};
   else cand = {0, 8};
+  // With a built handle (a full cache from an earlier tnmc_build_envs) the candidates are
+  // timed on `rows` rows in the middle of the lattice, rebuilt from the cached row below
+  // them: those rows carry the bond dimensions of the whole build, while the bottom rows'
+  // bonds are still small. (Not for MIXED, whose float64 carry between rows is not cached.)
+  const int L_min = *std::min_element(h->L.begin(), h->L.end());
+  const bool mid = h->built && h->cfg.ckpt_every == 0 && h->env_code != 2 && L_min >= 2 * rows + 2;
   cudaError_t e = launch_ingest(h->lay, d_J, h->stream);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&ev0);
@@ -391,10 +398,13 @@ tnmc_status tnmc_autotune_build(tnmc_handle *h, const float *d_J, int32_t rows, 
   for (size_t k = 0; k < cand.size() && e == cudaSuccess; ++k) {
     Layout l2 = h->lay;
     l2.variant = cand[k];
-    l2.tune_rows = 1;                                         // loads the kernel: not timed
     l2.dbg_logits = nullptr; l2.dbg_spectra = nullptr; l2.dbg_rowinfo = nullptr;
+    // an untimed one-row launch loads the kernel
+    if (mid) { l2.seg_begin = L_min / 2 - 1; l2.seg_end = L_min / 2; }
+    else l2.tune_rows = 1;
     e = launch_env_build(l2, h->env_code, h->plan.CH, h->stream);
-    l2.tune_rows = rows;
+    if (mid) { l2.seg_begin = L_min / 2 - rows; l2.seg_end = L_min / 2; }
+    else l2.tune_rows = rows;
     if (e == cudaSuccess) e = cudaEventRecord(ev0, h->stream);
     if (e == cudaSuccess) e = launch_env_build(l2, h->env_code, h->plan.CH, h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev1, h->stream);

@@ -177,6 +177,7 @@ __device__ __forceinline__ void rotate(dfloat &a, dfloat &b, dfloat cs, dfloat s
 
 // the column-norm comparison of the pivoted QR (float64, or the leading word of a double-float)
 __device__ __forceinline__ double pivot_key(double v) { return v; }
+__device__ __forceinline__ float pivot_key(float v) { return v; }
 __device__ __forceinline__ float pivot_key(dfloat v) { return v.hi; }
 
 template <typename T, int W>
@@ -208,7 +209,7 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
   const int hw = ht >> 5, lane = ht & 31;
   const int kq = min(m, n);
   if constexpr (PIVOT) {
-    static_assert(sizeof(T) == 8, "pivoted QR is the float64 and double-float preconditioner");
+    static_assert(sizeof(T) == 8 || std::is_same<T, float>::value, "pivoted QR of the Jacobi preconditioner");
     constexpr int G = 8;
     const int grp = ht / G, gl = ht % G;
     for (int k0 = 0; k0 < n; k0 += 256 / G) {           // uniform trip count over the half
@@ -879,9 +880,13 @@ __device__ int jacobi_rows(T *B, int nr, int nc, int nu, int ldb, int half, int 
 //     row pair, 1 = 8 lanes;
 //   bit 4, float32 build (FP32, TF32, BF16) on pairs of CTAs where they fit (float32's
 //     default is one CTA per realization); bits 0-1 then choose its Jacobi as above
-//     (0 = 16 lanes on the whole CTA).
-// Every layout computes the same method; they differ in summation order only.
-enum : int32_t { VARIANT_PAIR_MASK = 3, VARIANT_ONE_CTA = 4, VARIANT_SINGLE_8 = 8, VARIANT_FP32_PAIRS = 16 };
+//     (0 = 16 lanes on the whole CTA);
+//   bit 5, float32 build: the Jacobi preconditioned by a pivoted QR, as float64 and
+//     double-float always are (fewer sweeps; the float32 Householder Q is orthogonal only to
+//     float32 rounding, so the float32 truncation is a little less accurate).
+// Every layout computes the same method; they differ in rounding only.
+enum : int32_t { VARIANT_PAIR_MASK = 3, VARIANT_ONE_CTA = 4, VARIANT_SINGLE_8 = 8, VARIANT_FP32_PAIRS = 16,
+                 VARIANT_FP32_QRPRE = 32 };
 
 template <typename TC>
 __device__ __forceinline__ int jacobi_in_pair(int variant, TC *B, int nr, int nc, int nu, int ldb, int tid,
@@ -997,9 +1002,11 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   // float64 and double-float preconditioning QR with column pivoting: per sector, the column
   // norms and the permutation (piv: position -> original column; ipiv: original column ->
   // position)
-  constexpr bool PIVQR = sizeof(TC) == 8;
-  __shared__ TC sh_cn[PIVQR ? 2 * CH : 1];
-  __shared__ int sh_piv[PIVQR ? 2 * CH : 1], sh_ipiv[PIVQR ? 2 * CH : 1];
+  // the pivoted QR that preconditions the Jacobi: always in float64 and double-float, in
+  // the float32 build when its layout asks (VARIANT_FP32_QRPRE; uniform over the CTA)
+  const bool qrpre = sizeof(TC) == 8 || (lay.variant & VARIANT_FP32_QRPRE);
+  __shared__ TC sh_cn[2 * CH];
+  __shared__ int sh_piv[2 * CH], sh_ipiv[2 * CH];
   __shared__ long long sh_key[2 * CH];   // ordering keys of the singular values
   __shared__ TC Bnrm[2 * CH];        // squared row norms cached by the Jacobi sweeps
   __shared__ TC sh_scl[4 * CH];      // Jacobi row scales (d, 1/d) of float64 rows, per sector
@@ -1359,20 +1366,15 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         // Jacobi on the triangular factor needs far fewer sweeps (8-9 against 18-25 on
         // graded test spectra reaching 1e-12..1e-20, same accuracy). Rows r_s .. k_s - 1
         // (rank <= N) are zero and never kept.
-        constexpr bool QRPRE = sizeof(TC) == 8;
-        const int r0 = QRPRE ? min(k0, N) : k0, r1 = QRPRE ? min(k1, N) : k1;
-        if (QRPRE) {
+        const int r0 = qrpre ? min(k0, N) : k0, r1 = qrpre ? min(k1, N) : k1;
+        if (qrpre) {
           const int ks = half ? k1 : k0, rs = half ? r1 : r0;
           TC *As = Th + int64_t(half ? k0 : 0) * LDT;
           TC *ts = tau + half * CH;
           TC *Qb = US + half * P::CH2;   // free until this site's U S is written
-          if constexpr (PIVQR) {
-            householder_qr_strided<TC, LDT, 1, true>(As, ks, N, ts, half, ht, sh_cn + half * CH,
-                                                     sh_piv + half * CH);
-            for (int b = ht; b < N; b += 256) sh_ipiv[half * CH + sh_piv[half * CH + b]] = b;
-          } else {
-            householder_qr_strided<TC, LDT, 1>(As, ks, N, ts, half, ht);
-          }
+          householder_qr_strided<TC, LDT, 1, true>(As, ks, N, ts, half, ht, sh_cn + half * CH,
+                                                   sh_piv + half * CH);
+          for (int b = ht; b < N; b += 256) sh_ipiv[half * CH + sh_piv[half * CH + b]] = b;
           // the reflectors to Q's column-major buffer, R's lower part cleared
           for (int e = ht; e < ks * rs; e += 256) {
             const int i = e / rs, j = e % rs;
@@ -1584,7 +1586,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           if (a < nk && b < N) {
             const int i = sh_src[a];
             // pivoted preconditioning: column b of the site sits at position ipiv[b] of the rows
-            const int bb = PIVQR ? sh_ipiv[(i >= k0 ? CH : 0) + b] : b;
+            const int bb = qrpre ? sh_ipiv[(i >= k0 ? CH : 0) + b] : b;
             v = Th[int64_t(i) * LDT + bb] * Bnrm[i];
           }
           dst[e] = TS(v);

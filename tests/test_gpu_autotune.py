@@ -16,7 +16,7 @@ from oracle import bmps  # noqa: E402
 import parity  # noqa: E402
 
 CANDIDATES = [0, 1, 2, 4, 12]
-CANDIDATES_FP32 = [0, 8, 16, 17, 18]   # one CTA (4 or 8 lanes), or pairs of CTAs (bit 4)
+CANDIDATES_FP32 = [0, 8, 16, 17, 18, 32, 40]   # one CTA (4 or 8 lanes), pairs (bit 4), QR preconditioning (bit 5)
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +57,8 @@ def test_every_layout_matches_the_oracle(P, prec, variant):
 @pytest.mark.parametrize("variant", CANDIDATES_FP32)
 def test_every_float32_layout_matches_the_oracle(P, variant):
     # float32: |d log Z| / L^2 <= 1e-6 (where cut gaps are wide, beta = 1) and every draw the
-    # oracle's outside the float32 band; the pair layouts move sector 1's Jacobi to a second SM
+    # oracle's outside the float32 band; the pair layouts move sector 1's Jacobi to a second SM,
+    # bit 5 preconditions the Jacobi with a pivoted QR
     Ls, chi, beta, S = [9, 6, 12, 16], 8, 1.0, 40
     reals = parity.realizations(Ls, "pmj")
     t = P.TNMC(Ls, chi, beta, "fp32", max_samples=S)
@@ -79,7 +80,7 @@ def test_every_float32_layout_matches_the_oracle(P, variant):
 
 def test_bad_layout_refused(P):
     t = P.TNMC([4], 4, 1.0, "fp64", max_samples=4)
-    for bad in (3, -1, 32, 19):
+    for bad in (3, -1, 64, 19):
         with pytest.raises(P.TnmcError):
             t.set_build_variant(bad)
 
@@ -110,3 +111,37 @@ def test_autotuner_keeps_the_fastest_layout(P):
         full[v] = best
     chosen = min(times, key=times.get)
     assert full[chosen] <= 1.25 * min(full.values()), (times, full)
+
+
+def test_autotuner_on_a_built_handle_times_middle_rows(P):
+    # after a full build the candidates are timed on rows from the middle of the lattice
+    # (rebuilt from the cached row below them); the kept layout is within timing noise of
+    # the fastest full build, and the handle rebuilt with it meets the oracle
+    Ls, chi, beta = [48] * 6, 32, 1.0
+    reals = parity.realizations(Ls, "pmj")
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    t = P.TNMC(Ls, chi, beta, "fp32", max_samples=8)
+    t.build_envs(J)
+    times = t.autotune(J, rows=6)
+    assert sorted(times) == sorted(CANDIDATES_FP32)
+    chosen = min(times, key=times.get)
+    assert t.build_variant == chosen
+    full = {}
+    for v in CANDIDATES_FP32:
+        t.set_build_variant(v)
+        best = float("inf")
+        for _ in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(t.stream)
+            t.build_envs(J)
+            e1.record(t.stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        full[v] = best
+    assert full[chosen] <= 1.25 * min(full.values()), (times, full)
+    t.set_build_variant(chosen)
+    t.build_envs(J)
+    lz = t.log_z().cpu().numpy()
+    envs = parity.oracle_envs(reals[:2], beta, chi, t.cutoff)
+    for n in range(2):
+        assert abs(lz[n] - bmps.log_z(envs[n])) / (Ls[n] ** 2) <= 1e-6
