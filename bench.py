@@ -413,12 +413,8 @@ def run_ours(args, wl):
     n_mine = len(ids)
     # the build layout: the autotuner times the candidates on the bottom rows of these
     # realizations (setup, outside the timed region)
-    # (the Potts build has one layout: nothing to tune). A full build first, so the autotuner
-    # times rows from the middle of the lattice, whose bonds are those of the whole build
-    tune = {}
-    if args.tune_rows > 0 and wl.q == 2:
-        t.build_envs(J)
-        tune = t.autotune(J, rows=args.tune_rows)
+    # (the Potts build has one layout: nothing to tune)
+    tune = t.autotune(J, rows=args.tune_rows) if args.tune_rows > 0 and wl.q == 2 else {}
     stream = t.stream
     learned = None
     if args.learned:
@@ -564,13 +560,13 @@ def run_ours(args, wl):
         else:
             peak, peak_src = peaks_alu["fp64"], "measured: cuBLAS float64 GEMM on this GPU"
         proposals = n_mine * S * args.steps
-        # DRAM bytes per launch of the float32, chi = 64 build: an ncu capture of 8
-        # realizations at L = 128 (131072 site-rows) read + wrote 2.203 GB; traffic grows
-        # with the site-rows written
+        # DRAM bytes per launch of the float32, chi = 64 build in its preconditioned 8-lane
+        # layout (variant 40): an ncu capture of 8 realizations at L = 128 (131072 site-rows)
+        # read + wrote 2.181 GB; traffic grows with the site-rows written
         site_rows = sum(L * L for L in my_Ls)
-        if args.prec == "fp32" and plan_ch == 64 and not ckpt:
-            traffic = 2.203e9 / 131072 * site_rows
-            traffic_src = "ncu capture at L=128 x 8 realizations, scaled by site-rows"
+        if args.prec == "fp32" and plan_ch == 64 and not ckpt and variant_primary == 40:
+            traffic = 2.181e9 / 131072 * site_rows
+            traffic_src = "ncu capture at L=128 x 8 realizations (layout 40), scaled by site-rows"
         else:
             traffic, traffic_src = None, "no capture of this instantiation"
         # sampler: algorithmic bytes per sample-site = the right environment spilled and read
@@ -835,6 +831,8 @@ def run_env_once(args, wl):
     import paper_2509_19006_b300 as P
     J = torch.from_numpy(wl.packed_J()).cuda()
     t = P.TNMC(wl.Ls, wl.chi, wl.beta, args.prec, max_samples=wl.S, cutoff=args.cutoff, q=wl.q)
+    if args.build_variant >= 0:
+        t.set_build_variant(args.build_variant)
     t.build_envs(J)
     lz = t.log_z()
     torch.cuda.synchronize()
@@ -858,8 +856,11 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--ref-acceptance", type=float, default=None,
                     help="acceptance credited to the oracle (default: the measured value for the workload)")
-    ap.add_argument("--tune-rows", type=int, default=12,
-                    help="bottom rows the build autotuner times per layout (0: no autotuning)")
+    ap.add_argument("--tune-rows", type=int, default=6,
+                    help="rows below the lattice's middle the build autotuner times per layout "
+                         "(0: no autotuning)")
+    ap.add_argument("--build-variant", type=int, default=-1,
+                    help="--env-once: build with this layout (tnmc_set_build_variant) instead of the default")
     ap.add_argument("--arms", default=None,
                     help="comparison arms 'prec:steps,...' timed after the primary line (default for "
                          "the L256 workload: fp64:1,dfloat:2; '' for none)")

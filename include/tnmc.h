@@ -404,11 +404,12 @@ int32_t tnmc_get_build_variant(const tnmc_handle *h);
 /* Autotuner of the build layout (the paper has no counterpart): ingests d_J (as
  * tnmc_build_envs), then for each candidate layout of the handle's precision builds
  * `rows` rows of every realization, timed with CUDA events on the handle's stream, and
- * keeps the fastest for later builds. On a handle that has been built (and holds every
- * row: no checkpoints, not TNMC_MIXED) the timed rows are the `rows` rows below the
- * middle of the smallest lattice, rebuilt from the cached row under them, whose bond
- * dimensions are those of the whole build; otherwise the bottom `rows` rows, whose bonds
- * are smaller. h_variants / h_ms (host, optional, capacity *h_count on entry) receive the
+ * keeps the fastest for later builds. The timed rows are the `rows` rows below the
+ * middle of the smallest lattice, rebuilt from the cached row under them (their bond
+ * dimensions are those of the whole build); the rows from the middle down are built once
+ * first, untimed, unless the handle holds a full build. With checkpoints, for TNMC_MIXED,
+ * or for lattices below 2 rows + 2, the bottom `rows` rows are timed instead (their bonds
+ * are smaller). h_variants / h_ms (host, optional, capacity *h_count on entry) receive the
  * candidates and their times in ms; *h_count receives the number of candidates.
  * Synchronises the stream. The timing launches overwrite rows of the cache, so the
  * handle must be built again (tnmc_build_envs) before proposals.

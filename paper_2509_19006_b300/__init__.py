@@ -409,8 +409,10 @@ class TNMC:
 
     @_on_stream
     def autotune(self, J, rows: int = 12):
-        """Time the candidate build layouts on the bottom `rows` rows of these realizations
-        and keep the fastest; returns {variant: ms}. Build again before proposing."""
+        """Time the candidate build layouts on `rows` rows below the middle of these lattices
+        (rebuilt from the cached row under them; the rows beneath are built first unless the
+        handle is built) and keep the fastest; returns {variant: ms}. Build again before
+        proposing."""
         import numpy as np
         assert J.dtype == self.torch.float32 and J.is_cuda and J.is_contiguous()
         cap = 16

@@ -383,13 +383,22 @@ tnmc_status tnmc_autotune_build(tnmc_handle *h, const float *d_J, int32_t rows, 
   else if (h->env_code == 1)   // one CTA, or pairs (bit 4); with or without the QR preconditioning (bit 5)
     cand = {0, 8, 16, 16 | 1, 16 | 2, 32, 32 | 8};
   else cand = {0, 8};
-  // With a built handle (a full cache from an earlier tnmc_build_envs) the candidates are
-  // timed on `rows` rows in the middle of the lattice, rebuilt from the cached row below
-  // them: those rows carry the bond dimensions of the whole build, while the bottom rows'
-  // bonds are still small. (Not for MIXED, whose float64 carry between rows is not cached.)
+  // The candidates are timed on the `rows` rows below the middle of the smallest lattice,
+  // rebuilt from the cached row under them: those rows carry the bond dimensions of the
+  // whole build, while the bottom rows' bonds are still small. The rows from the middle
+  // down are built once first (untimed) unless the handle holds a full build already.
+  // (Not with checkpoints, nor for MIXED, whose float64 carry between rows is not cached:
+  // there the bottom rows are timed.)
   const int L_min = *std::min_element(h->L.begin(), h->L.end());
-  const bool mid = h->built && h->cfg.ckpt_every == 0 && h->env_code != 2 && L_min >= 2 * rows + 2;
+  const bool mid = h->cfg.ckpt_every == 0 && h->env_code != 2 && L_min >= 2 * rows + 2;
   cudaError_t e = launch_ingest(h->lay, d_J, h->stream);
+  if (e == cudaSuccess && mid && !h->built) {
+    Layout l0 = h->lay;
+    l0.dbg_logits = nullptr; l0.dbg_spectra = nullptr; l0.dbg_rowinfo = nullptr;
+    l0.seg_begin = L_min / 2;
+    l0.seg_end = h->plan.L_max;   // every realization from its bottom row up to the middle
+    e = launch_env_build(l0, h->env_code, h->plan.CH, h->stream);
+  }
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&ev1);
