@@ -267,3 +267,40 @@ def test_trained_correction_gains_over_plain_small_chi(P):
     small.set_correction(None)
     print(f"KL per site {kl0:.4g} -> {kl1:.4g}; acceptance {a0:.4f} -> {a1:.4f}")
     assert a1 > a0, (a0, a1)
+
+
+def test_trained_correction_lowers_kl_at_L64(P):
+    """At L = 64 (16 Gaussian realizations, beta = 2, chi = 2 corrected towards chi = 8) the
+    trained network still moves the chi = 2 conditionals towards chi = 8's: the held-out
+    per-site KL divergence drops by more than 10 % (measured 14 %). The acceptance of either
+    proposal is of order 1e-3 at this size, too small to compare (design notes)."""
+    Ls, beta, S = [64] * 16, 2.0, 256
+    reals = parity.realizations(Ls, "gauss", base_seed=5000)
+    J = torch.from_numpy(parity.packed_J(reals)).cuda()
+    small = P.TNMC(Ls, 2, beta, "fp64", max_samples=S)
+    big = P.TNMC(Ls, 8, beta, "fp64", max_samples=S)
+    small.build_envs(J)
+    big.build_envs(J)
+
+    def data(base):
+        props = big.propose(S, 7, base)
+        _, _, lg_s = small.score_logits(props.spins, S)
+        _, _, lg_b = big.score_logits(props.spins, S)
+        return small.mlp_features(props.spins, lg_s, S), lg_b
+
+    feat, tgt = data(0)
+    feat_te, tgt_te = data(10_000)
+
+    def kl(delta):
+        z = feat_te[:, 0].double() + delta.double()
+        zb = tgt_te.double()
+        pb = torch.sigmoid(zb)
+        ls = torch.nn.functional.logsigmoid
+        return (pb * (ls(zb) - ls(z)) + (1 - pb) * (ls(-zb) - ls(-z))).mean().item()
+
+    net = P.MLP(seed=3)
+    kl0 = kl(torch.zeros_like(tgt_te))
+    net.train(feat, tgt, steps=3000, batch=65536, lr=3e-3, lr_final=3e-4, seed=1)
+    kl1 = kl(net.forward(feat_te))
+    print(f"L=64: KL per site {kl0:.4g} -> {kl1:.4g}")
+    assert kl1 < 0.9 * kl0, (kl0, kl1)
