@@ -115,8 +115,10 @@ typedef struct {
                             in float64 (the precision the build carries between rows). */
   int32_t q_states;      /* 0 or 2: the Ising model of Eq. 1 (every mode above). 3 or 4: the
                             q-state Potts extension (Sec. 5), E = -sum J_ij delta(s_i, s_j) with
-                            states 0 .. q-1 stored one byte per site; float64 only (prec =
-                            TNMC_FP64), chi <= 16 with q^2 chi <= 144, no checkpoints, no
+                            states 0 .. q-1 stored one byte per site; prec = TNMC_FP64 or
+                            TNMC_FP32 (build, cache and sampling contractions in that type; the
+                            per-draw probabilities, log q and energies in float64), chi <= 16
+                            with q^2 chi <= 144, no checkpoints, no
                             learned correction. Proposals draw the first state k with
                             u < p_0 + ... + p_k (float64 partial sums, the site's Philox uniform).
                             Entry points other than build_envs, log_z, propose, score,

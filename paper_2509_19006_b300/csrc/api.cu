@@ -32,12 +32,12 @@ int64_t static_scratch_bytes();
 int64_t sampler_smem_bytes(int prec, int CH, int L_max);
 cudaError_t launch_mlp_features(const Layout &lay, int S, int L_max, const uint8_t *spins,
                                 const float *logits, float *feat, cudaStream_t st);
-int64_t potts_slot_bytes(int L_max);
+int64_t potts_slot_bytes(int L_max, int esz);
 bool potts_supported(int q, int chi);
 int potts_scratch_ch();
-cudaError_t launch_potts_build(const Layout &lay, int q, cudaStream_t st);
-cudaError_t launch_potts_log_z(const Layout &lay, int q, double *logz, cudaStream_t st);
-cudaError_t launch_potts_sample(const Layout &lay, int q, int S, uint64_t seed, uint64_t base,
+cudaError_t launch_potts_build(const Layout &lay, int q, int prec, cudaStream_t st);
+cudaError_t launch_potts_log_z(const Layout &lay, int q, int prec, double *logz, cudaStream_t st);
+cudaError_t launch_potts_sample(const Layout &lay, int q, int prec, int S, uint64_t seed, uint64_t base,
                                 const uint8_t *in, uint8_t *out, double *lq, double *E, cudaStream_t st);
 }  // namespace tnmc
 
@@ -75,7 +75,8 @@ tnmc_status check_cfg(const tnmc_config *cfg) {
   if (cfg->prec < TNMC_FP64 || cfg->prec > TNMC_DFLOAT) return TNMC_ERR_ARG;
   if (cfg->q_states < 0 || cfg->q_states == 1) return TNMC_ERR_ARG;
   if (cfg->q_states > 2) {   // the q-state Potts extension: float64 kernels with fixed panel bounds
-    if (cfg->prec != TNMC_FP64 || cfg->ckpt_every != 0 || !potts_supported(cfg->q_states, cfg->chi))
+    if ((cfg->prec != TNMC_FP64 && cfg->prec != TNMC_FP32) || cfg->ckpt_every != 0 ||
+        !potts_supported(cfg->q_states, cfg->chi))
       return TNMC_ERR_UNSUPPORTED;
   }
   for (int n = 0; n < cfg->n_real; ++n)
@@ -135,7 +136,8 @@ Plan make_plan(const tnmc_config *cfg) {
   p.off_bonds = take(p.sum_bonds * 8);
   p.off_lam = take(p.sum_L * 8);
   p.env_slots = std::min(cfg->n_real, kEnvSlots);
-  p.env_slot = potts ? potts_slot_bytes(p.L_max) : env_slot_bytes(env_mode(cfg->prec), p.CH, p.L_max, cfg->chi);
+  p.env_slot = potts ? potts_slot_bytes(p.L_max, int(esz))
+                     : env_slot_bytes(env_mode(cfg->prec), p.CH, p.L_max, cfg->chi);
   p.env_bytes = p.env_slot * p.env_slots;
   p.off_env = take(p.env_bytes);
   p.samp_bytes = int64_t(cfg->max_samples) * p.sum_L * p.CH * esz;
@@ -444,7 +446,7 @@ tnmc_status tnmc_build_envs(tnmc_handle *h, const float *d_J) {
   if (!h || !d_J) return TNMC_ERR_ARG;
   cudaError_t e = launch_ingest(h->lay, d_J, h->stream);
   if (h->q > 2) {
-    if (e == cudaSuccess) e = launch_potts_build(h->lay, h->q, h->stream);
+    if (e == cudaSuccess) e = launch_potts_build(h->lay, h->q, h->prec_code, h->stream);
     if (e != cudaSuccess) return TNMC_ERR_CUDA;
     h->built = true;
     return TNMC_OK;
@@ -462,7 +464,8 @@ tnmc_status tnmc_log_z(tnmc_handle *h, double *d_logz) {
   if (!h || !d_logz) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
   if (h->q > 2)
-    return launch_potts_log_z(h->lay, h->q, d_logz, h->stream) == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
+    return launch_potts_log_z(h->lay, h->q, h->prec_code, d_logz, h->stream) == cudaSuccess ? TNMC_OK
+                                                                                           : TNMC_ERR_CUDA;
   return launch_log_z(h->lay, h->prec_code, d_logz, h->stream) == cudaSuccess ? TNMC_OK
                                                                                : TNMC_ERR_CUDA;
 }
@@ -473,8 +476,8 @@ tnmc_status tnmc_propose(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
   if (S < 1 || S > h->cfg.max_samples) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
   if (h->q > 2)
-    return launch_potts_sample(h->lay, h->q, S, seed, prop_base, nullptr, d_spins, d_logq, d_E,
-                               h->stream) == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
+    return launch_potts_sample(h->lay, h->q, h->prec_code, S, seed, prop_base, nullptr, d_spins, d_logq,
+                               d_E, h->stream) == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
   return for_segments(h, [&](const Layout &l) {
            return launch_propose(l, h->prec_code, h->plan.CH, S, seed, prop_base, d_spins, d_logq,
                                  d_E, h->stream);
@@ -508,8 +511,8 @@ tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins, double
   if (S < 1 || S > h->cfg.max_samples) return TNMC_ERR_ARG;
   if (!h->built) return TNMC_ERR_STATE;
   if (h->q > 2)
-    return launch_potts_sample(h->lay, h->q, S, 0, 0, d_spins, nullptr, d_logq, d_E, h->stream) ==
-                   cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
+    return launch_potts_sample(h->lay, h->q, h->prec_code, S, 0, 0, d_spins, nullptr, d_logq, d_E,
+                               h->stream) == cudaSuccess ? TNMC_OK : TNMC_ERR_CUDA;
   return for_segments(h, [&](const Layout &l) {
            return launch_score(l, h->prec_code, h->plan.CH, S, d_spins, d_logq, d_E, h->stream);
          }) == cudaSuccess

@@ -1,6 +1,8 @@
 // q-state Potts extension (Sec. 5: the method carries over to Potts models with the
-// physical index of every tensor widened to q states), float64, batched over
-// realizations x samples like the Ising path:
+// physical index of every tensor widened to q states), in float64 or float32 (the element
+// type T of the build, the cache and the sampling contractions; per-draw probabilities, log
+// scales, log q and energies are float64), batched over realizations x samples like the
+// Ising path:
 //   E(s) = - sum_<ij> J_ij delta(s_i, s_j),  s_i in {0 .. q-1}.
 // There is no parity form here (the Z2 symmetry of the Ising model has no q-state
 // analogue that halves the storage), so every site is a dense chi x q x chi tensor,
@@ -47,11 +49,11 @@ struct PottsSmem {
   static constexpr int oU = oT + PD * PLDT;        // U S (row-major, ld PCH)
   static constexpr int oTau = oU + PD * PCH;
   static constexpr int oSn = oTau + PD;
-  static constexpr int n = oSn + PD;
-  static constexpr int bytes = n * 8;
+  static constexpr int n = oSn + PD;   // values of the element type
 };
 
-__device__ __forceinline__ double pwarp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T pwarp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -64,32 +66,33 @@ __device__ __forceinline__ double pweight(double beta, double J, bool same) {
 
 // Householder QR of the m x n column-major panel A (ld PM) by the whole CTA (LAPACK's
 // geqr2 scheme, beta = -sign(x0) |x|; reflectors below the diagonal with v_j = 1 implied).
-__device__ void p_householder(double *A, int m, int n, double *tau) {
+template <typename T>
+__device__ void p_householder(T *A, int m, int n, T *tau) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int kq = min(m, n);
   for (int j = 0; j < kq; ++j) {
-    double *col = A + j * PM;
+    T *col = A + j * PM;
     if (warp == 0) {
-      double s2 = 0.0;
+      T s2 = T(0);
       for (int i = j + 1 + lane; i < m; i += 32) s2 += col[i] * col[i];
       s2 = pwarp_sum(s2);
-      const double x0 = col[j];
-      if (s2 == 0.0) {
-        if (lane == 0) tau[j] = 0.0;
+      const T x0 = col[j];
+      if (s2 == T(0)) {
+        if (lane == 0) tau[j] = T(0);
       } else {
-        const double mu = sqrt(x0 * x0 + s2);
-        const double be = x0 <= 0.0 ? mu : -mu;
-        const double sc = 1.0 / (x0 - be);
+        const T mu = sqrt(x0 * x0 + s2);
+        const T be = x0 <= T(0) ? mu : -mu;
+        const T sc = T(1) / (x0 - be);
         for (int i = j + 1 + lane; i < m; i += 32) col[i] *= sc;
         if (lane == 0) { tau[j] = (be - x0) / be; col[j] = be; }
       }
     }
     __syncthreads();
-    const double tj = tau[j];
-    if (tj != 0.0) {
+    const T tj = tau[j];
+    if (tj != T(0)) {
       for (int k = j + 1 + warp; k < n; k += PT / 32) {
-        double *ck = A + k * PM;
-        double w = lane == 0 ? ck[j] : 0.0;
+        T *ck = A + k * PM;
+        T w = lane == 0 ? ck[j] : T(0);
         for (int i = j + 1 + lane; i < m; i += 32) w += col[i] * ck[i];
         w = pwarp_sum(w) * tj;
         if (lane == 0) ck[j] -= w;
@@ -101,15 +104,16 @@ __device__ void p_householder(double *A, int m, int n, double *tau) {
 }
 
 // Explicit Q (m x kq) in place of the reflectors (LAPACK's org2r order).
-__device__ void p_form_q(double *A, const double *tau, int m, int kq) {
+template <typename T>
+__device__ void p_form_q(T *A, const T *tau, int m, int kq) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int j = kq - 1; j >= 0; --j) {
-    const double tj = tau[j];
-    const double *v = A + j * PM;
-    if (tj != 0.0) {
+    const T tj = tau[j];
+    const T *v = A + j * PM;
+    if (tj != T(0)) {
       for (int l = j + 1 + warp; l < kq; l += PT / 32) {
-        double *ql = A + l * PM;
-        double w = lane == 0 ? ql[j] : 0.0;
+        T *ql = A + l * PM;
+        T w = lane == 0 ? ql[j] : T(0);
         for (int i = j + 1 + lane; i < m; i += 32) w += v[i] * ql[i];
         w = pwarp_sum(w) * tj;
         if (lane == 0) ql[j] -= w;
@@ -118,10 +122,10 @@ __device__ void p_form_q(double *A, const double *tau, int m, int kq) {
     }
     __syncthreads();
     if (warp == 0) {
-      double *qj = A + j * PM;
+      T *qj = A + j * PM;
       for (int i = lane; i < m; i += 32) {
-        if (i < j) qj[i] = 0.0;
-        else if (i == j) qj[i] = 1.0 - tj;
+        if (i < j) qj[i] = T(0);
+        else if (i == j) qj[i] = T(1) - tj;
         else qj[i] = -tj * qj[i];
       }
     }
@@ -134,11 +138,12 @@ __device__ void p_form_q(double *A, const double *tau, int m, int kq) {
 // column of largest norm below row j (ties: lower index) is swapped into place; R ends in
 // the upper triangle, the reflectors below it, piv[k] = the original index of column k.
 // The column norms below the current row are recomputed exactly in every update pass.
-__device__ void p_qr_pivot_rows(double *A, int m, int n, double *tau, double *cn, int *piv) {
+template <typename T>
+__device__ void p_qr_pivot_rows(T *A, int m, int n, T *tau, T *cn, int *piv) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int kq = min(m, n);
   for (int k = warp; k < n; k += PT / 32) {
-    double s2 = 0.0;
+    T s2 = T(0);
     for (int i = lane; i < m; i += 32) s2 += A[i * PLDT + k] * A[i * PLDT + k];
     s2 = pwarp_sum(s2);
     if (lane == 0) { cn[k] = s2; piv[k] = k; }
@@ -146,52 +151,52 @@ __device__ void p_qr_pivot_rows(double *A, int m, int n, double *tau, double *cn
   __syncthreads();
   for (int j = 0; j < kq; ++j) {
     if (warp == 0) {
-      double best = -1.0;
+      T best = T(-1);
       int bk = j;
       for (int k = j + lane; k < n; k += 32)
         if (cn[k] > best) { best = cn[k]; bk = k; }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
         if (ob > best || (ob == best && ok < bk)) { best = ob; bk = ok; }
       }
       if (bk != j) {
         for (int i = lane; i < m; i += 32) {
-          const double x = A[i * PLDT + j];
+          const T x = A[i * PLDT + j];
           A[i * PLDT + j] = A[i * PLDT + bk];
           A[i * PLDT + bk] = x;
         }
         if (lane == 0) {
-          const double c = cn[j]; cn[j] = cn[bk]; cn[bk] = c;
+          const T c = cn[j]; cn[j] = cn[bk]; cn[bk] = c;
           const int p = piv[j]; piv[j] = piv[bk]; piv[bk] = p;
         }
       }
       __syncwarp();
-      double s2 = 0.0;
+      T s2 = T(0);
       for (int i = j + 1 + lane; i < m; i += 32) s2 += A[i * PLDT + j] * A[i * PLDT + j];
       s2 = pwarp_sum(s2);
-      const double x0 = A[j * PLDT + j];
-      if (s2 == 0.0) {
-        if (lane == 0) tau[j] = 0.0;
+      const T x0 = A[j * PLDT + j];
+      if (s2 == T(0)) {
+        if (lane == 0) tau[j] = T(0);
       } else {
-        const double mu = sqrt(x0 * x0 + s2);
-        const double be = x0 <= 0.0 ? mu : -mu;
-        const double sc = 1.0 / (x0 - be);
+        const T mu = sqrt(x0 * x0 + s2);
+        const T be = x0 <= T(0) ? mu : -mu;
+        const T sc = T(1) / (x0 - be);
         for (int i = j + 1 + lane; i < m; i += 32) A[i * PLDT + j] *= sc;
         if (lane == 0) { tau[j] = (be - x0) / be; A[j * PLDT + j] = be; }
       }
     }
     __syncthreads();
-    const double tj = tau[j];
+    const T tj = tau[j];
     for (int k = j + 1 + warp; k < n; k += PT / 32) {
-      double w = lane == 0 ? A[j * PLDT + k] : 0.0;
+      T w = lane == 0 ? A[j * PLDT + k] : T(0);
       for (int i = j + 1 + lane; i < m; i += 32) w += A[i * PLDT + j] * A[i * PLDT + k];
       w = pwarp_sum(w) * tj;
       if (lane == 0) A[j * PLDT + k] -= w;
-      double nn = 0.0;
+      T nn = T(0);
       for (int i = j + 1 + lane; i < m; i += 32) {
-        const double x = A[i * PLDT + k] - w * A[i * PLDT + j];
+        const T x = A[i * PLDT + k] - w * A[i * PLDT + j];
         A[i * PLDT + k] = x;
         nn += x * x;
       }
@@ -227,6 +232,15 @@ __device__ __forceinline__ void p_rotation(double al, double be, double ga, doub
   sn = y * t;
 }
 
+// float32: the plain Jacobi rotation (float32 division and square root are cheap); c and
+// s form an exact rotation to float32 rounding.
+__device__ __forceinline__ void p_rotation(float al, float be, float ga, float &t, float &cs, float &sn) {
+  const float zeta = (be - al) / (2.f * ga);
+  t = fabsf(zeta) > 1e18f ? 0.5f / zeta : (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  cs = 1.f / sqrtf(1.f + t * t);
+  sn = cs * t;
+}
+
 // One-sided Jacobi on the nr rows of B (ld PLDT): inner products over the first nc
 // columns, rotations over nc + nu columns. Round-robin (circle) schedule, 16 lanes per
 // row pair. The squared row norms are measured exactly at the start of every sweep and
@@ -234,20 +248,23 @@ __device__ __forceinline__ void p_rotation(double al, double be, double ga, doub
 // product per pair. A pair is rotated while |gamma| > tol sqrt(alpha beta), tol = 8
 // sqrt(nc) eps, unless either row is below eps x the largest row (rounding noise).
 // Returns the sweeps taken.
-__device__ int p_jacobi(double *B, int nr, int nc, int nu, int *sh_flag, double *nrm2) {
+template <typename T>
+__device__ int p_jacobi(T *B, int nr, int nc, int nu, int *sh_flag, T *nrm2) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (nr <= 1) return 0;
   constexpr int TPP = 16;
   const int P = nr + (nr & 1), np = P / 2;
   const int g = tid / TPP, gl = tid % TPP;
-  const double eps = 1.1102230246251565e-16;
-  const double tol2 = 64.0 * eps * eps * double(nc > 4 ? nc : 4);
-  __shared__ double sh_mx;
+  // tol = 8 sqrt(nc) eps in float64, 4 sqrt(nc) eps in float32 (rows orthogonal closer to the
+  // rounding floor at float32's cheap rounds)
+  const T eps = T(Num<T>::eps());
+  const T tol2 = T(sizeof(T) == 4 ? 16 : 64) * eps * eps * T(nc > 4 ? nc : 4);
+  __shared__ T sh_mx;
   int sweep = 0;
   for (; sweep < P_MAX_SWEEPS; ++sweep) {
     // exact squared norms, one warp per row
     for (int i = warp; i < nr; i += PT / 32) {
-      double s2 = 0.0;
+      T s2 = T(0);
       for (int x = lane; x < nc; x += 32) s2 += B[i * PLDT + x] * B[i * PLDT + x];
       s2 = pwarp_sum(s2);
       if (lane == 0) nrm2[i] = s2;
@@ -255,12 +272,12 @@ __device__ int p_jacobi(double *B, int nr, int nc, int nu, int *sh_flag, double 
     if (tid == 0) *sh_flag = 0;
     __syncthreads();
     if (tid == 0 && sweep == 0) {
-      double mx = 0.0;
-      for (int i = 0; i < nr; ++i) mx = fmax(mx, nrm2[i]);
+      T mx = T(0);
+      for (int i = 0; i < nr; ++i) mx = nrm2[i] > mx ? nrm2[i] : mx;
       sh_mx = mx;
     }
     __syncthreads();
-    const double floor2 = sh_mx * eps * eps;
+    const T floor2 = sh_mx * eps * eps;
     for (int k = 0; k < P - 1; ++k) {
       int i = -1, j = -1;
       if (g < np) {
@@ -269,21 +286,21 @@ __device__ int p_jacobi(double *B, int nr, int nc, int nu, int *sh_flag, double 
         j = 1 + (p1 - 1 + k) % (P - 1);
         if (i >= nr || j >= nr) i = j = -1;
       }
-      double ga = 0.0;
+      T ga = T(0);
       if (i >= 0) {
-        const double *a = B + i * PLDT, *b = B + j * PLDT;
+        const T *a = B + i * PLDT, *b = B + j * PLDT;
         for (int x = gl; x < nc; x += TPP) ga += a[x] * b[x];
       }
 #pragma unroll
       for (int o = TPP / 2; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
       if (i >= 0) {
-        const double al = nrm2[i], be = nrm2[j];
+        const T al = nrm2[i], be = nrm2[j];
         if (al > floor2 && be > floor2 && ga * ga > tol2 * al * be) {
-          double t, cs, sn;
+          T t, cs, sn;
           p_rotation(al, be, ga, t, cs, sn);
-          double *a = B + i * PLDT, *b = B + j * PLDT;
+          T *a = B + i * PLDT, *b = B + j * PLDT;
           for (int x = gl; x < nc + nu; x += TPP) {
-            const double av = a[x], bv = b[x];
+            const T av = a[x], bv = b[x];
             a[x] = cs * av - sn * bv;
             b[x] = sn * av + cs * bv;
           }
@@ -300,30 +317,31 @@ __device__ int p_jacobi(double *B, int nr, int nc, int nu, int *sh_flag, double 
   return sweep + 1;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *W = (double *)smem_raw;
-  double *Ap = W + PottsSmem::oA, *Rb = W + PottsSmem::oR, *Cs = W + PottsSmem::oC;
-  double *Th = W + PottsSmem::oT, *US = W + PottsSmem::oU, *tau = W + PottsSmem::oTau;
-  double *sn = W + PottsSmem::oSn;
+  T *W = (T *)smem_raw;
+  T *Ap = W + PottsSmem::oA, *Rb = W + PottsSmem::oR, *Cs = W + PottsSmem::oC;
+  T *Th = W + PottsSmem::oT, *US = W + PottsSmem::oU, *tau = W + PottsSmem::oTau;
+  T *sn = W + PottsSmem::oSn;
   __shared__ double sh_red[PT / 32];
-  __shared__ double sh_nrm2[PD];   // Jacobi row norms
-  __shared__ double sh_cn[PD];     // column norms of the pivoted QR
+  __shared__ T sh_nrm2[PD];   // Jacobi row norms
+  __shared__ T sh_cn[PD];     // column norms of the pivoted QR
   __shared__ int sh_piv[PD], sh_ipiv[PD];
   __shared__ double sh_lam, sh_smax, sh_flops, sh_dsum;
   __shared__ int sh_n, sh_flag, sh_keep, sh_kprev, sh_sweeps, sh_svds;
   __shared__ long long sh_clk[4];   // cycles of the row: phase A, Theta products, Jacobi, selection + stores
   long long t_mark = 0;
   __shared__ int sh_src[PD];
-  __shared__ double sh_Bh[PQ * PQ], sh_Bv[PQ * PQ];
+  __shared__ T sh_Bh[PQ * PQ], sh_Bv[PQ * PQ];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int chi = lay.chi;
   const int64_t chi2 = int64_t(chi) * chi;
   const double beta = lay.beta;
   const int64_t site_vals = int64_t(q) * chi2;
   unsigned char *slot = (unsigned char *)lay.env_scratch + int64_t(blockIdx.x) * lay.env_slot_bytes;
-  double *Qstore = (double *)slot;                                     // L_max panels PM x PD
-  int2 *info = (int2 *)(slot + align256(int64_t(lay.L_max) * PM * PD * 8));   // (kprev, kq) per site
+  T *Qstore = (T *)slot;                                               // L_max panels PM x PD
+  int2 *info = (int2 *)(slot + align256(int64_t(lay.L_max) * PM * PD * sizeof(T)));   // (kprev, kq) per site
 
   for (;;) {
     if (tid == 0) sh_n = atomicAdd(lay.counter, 1);
@@ -336,14 +354,14 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
     const int L = ri.L;
     if (lay.flags[n] & FLAG_BAD_J) continue;   // uniform
     const float *jr = lay.jr + ri.site_off, *jd = lay.jd + ri.site_off;
-    double *cache_n = (double *)lay.cache + ri.cache_off * site_vals;
+    T *cache_n = (T *)lay.cache + ri.cache_off * site_vals;
     int2 *bonds_n = lay.bonds + ri.bond_off;
     if (tid == 0) sh_lam = 0.0;
     for (int r = L - 1; r >= 0; --r) {
       const bool bottom = (r == L - 1);
-      const double *prev = bottom ? nullptr : cache_n + int64_t(r + 1) * L * site_vals;
+      const T *prev = bottom ? nullptr : cache_n + int64_t(r + 1) * L * site_vals;
       const int2 *bprev = bottom ? nullptr : bonds_n + int64_t(r + 1) * (L + 1);
-      double *dst_row = cache_n + int64_t(r) * L * site_vals;
+      T *dst_row = cache_n + int64_t(r) * L * site_vals;
       // row constants: the normalisations of the row's Boltzmann matrices
       {
         double acc = 0.0;
@@ -359,7 +377,7 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           for (int w = 0; w < PT / 32; ++w) s += sh_red[w];
           sh_lam += s;
           sh_kprev = 1;
-          Rb[0] = 1.0;
+          Rb[0] = T(1);
           sh_flops = 0.0; sh_dsum = 0.0; sh_sweeps = 0; sh_svds = 0;
           for (int f = 0; f < 4; ++f) sh_clk[f] = 0;
           t_mark = clock64();
@@ -374,19 +392,19 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
         const int kprev = sh_kprev;
         if (tid < q * q) {
           const int a = tid / q, b = tid % q;
-          sh_Bh[tid] = last ? 1.0 : pweight(beta, (double)jr[r * L + c], a == b);
-          sh_Bv[tid] = bottom ? 0.0 : pweight(beta, (double)jd[r * L + c], a == b);
+          sh_Bh[tid] = T(last ? 1.0 : pweight(beta, (double)jr[r * L + c], a == b));
+          sh_Bv[tid] = T(bottom ? 0.0 : pweight(beta, (double)jd[r * L + c], a == b));
         }
         __syncthreads();
         // C[s][a'][b'] = sum_n Bv[s, n] A_c[n][a'][b'] of the row below (1 on the bottom row)
         for (int e = tid; e < q * Dl * Dr; e += PT) {
           const int s = e / (Dl * Dr), rem = e % (Dl * Dr), a = rem / Dr, b = rem % Dr;
-          double acc;
+          T acc;
           if (bottom) {
-            acc = 1.0;
+            acc = T(1);
           } else {
-            acc = 0.0;
-            const double *site = prev + int64_t(c) * site_vals;
+            acc = T(0);
+            const T *site = prev + int64_t(c) * site_vals;
             for (int nn = 0; nn < q; ++nn) acc += sh_Bv[s * q + nn] * site[(int64_t(nn) * chi + a) * chi + b];
           }
           Cs[(s * PCH + a) * PCH + b] = acc;
@@ -397,11 +415,11 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
         for (int e = tid; e < m * ncol; e += PT) {
           const int row = e / ncol, col = e % ncol;
           const int k = row / q, s = row % q, b = col / Dr, bb = col % Dr;
-          double acc = 0.0;
+          T acc = T(0);
           if (c == 0) {
             acc = Cs[(s * PCH + 0) * PCH + bb];
           } else {
-            const double *Rk = Rb + k * PD + s * Dl;
+            const T *Rk = Rb + k * PD + s * Dl;
             for (int a = 0; a < Dl; ++a) acc += Rk[a] * Cs[(s * PCH + a) * PCH + bb];
           }
           Ap[row + col * PM] = sh_Bh[s * q + b] * acc;
@@ -415,7 +433,7 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           double acc = 0.0;
           for (int e = tid; e < kq * ncol; e += PT) {
             const int i = e / ncol, b = e % ncol;
-            if (b >= i) { const double v = Ap[i + b * PM]; acc += v * v; }
+            if (b >= i) { const double v = double(Ap[i + b * PM]); acc += v * v; }
           }
           acc = pwarp_sum(acc);
           if (lane == 0) sh_red[warp] = acc;
@@ -424,10 +442,10 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           for (int w = 0; w < PT / 32; ++w) nrm2 += sh_red[w];
           const double nrm = sqrt(nrm2);
           const bool ok = nrm > 0.0 && isfinite(nrm);
-          const double inv = ok ? 1.0 / nrm : 0.0;
+          const T inv = ok ? T(1.0 / nrm) : T(0);
           for (int e = tid; e < kq * ncol; e += PT) {
             const int i = e / ncol, b = e % ncol;
-            Rb[i * PD + b] = (b >= i) ? Ap[i + b * PM] * inv : 0.0;
+            Rb[i * PD + b] = (b >= i) ? Ap[i + b * PM] * inv : T(0);
           }
           if (tid == 0) {
             if (ok) sh_lam += log(nrm);
@@ -436,7 +454,7 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
         }
         __syncthreads();
         p_form_q(Ap, tau, m, kq);
-        double *qs = Qstore + int64_t(c) * PM * PD;
+        T *qs = Qstore + int64_t(c) * PM * PD;
         for (int e = tid; e < m * kq; e += PT) {
           const int col = e / m, i = e % m;
           qs[i + col * PM] = Ap[i + col * PM];
@@ -464,21 +482,21 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           }
         } else {
           const int kq = info[c].y;
-          const double *qs = Qstore + int64_t(c) * PM * PD;
+          const T *qs = Qstore + int64_t(c) * PM * PD;
           for (int e = tid; e < Dl * nc; e += PT) {
             const int a = e / nc, col = e % nc, s = col / kr, j = col % kr;
-            double acc = 0.0;
+            T acc = T(0);
             for (int p = 0; p < kq; ++p) acc += qs[(a * q + s) + p * PM] * US[p * PCH + j];
             Th[a * PLDT + col] = acc;
           }
         }
         __syncthreads();
         if (tid == 0) { const long long t1 = clock64(); sh_clk[1] += t1 - t_mark; t_mark = t1; }
-        double *site_dst = dst_row + int64_t(c) * site_vals;
+        T *site_dst = dst_row + int64_t(c) * site_vals;
         if (c == 0) {
           // site 0 (left bond 1): divided by its norm
           double acc = 0.0;
-          for (int x = tid; x < nc; x += PT) acc += Th[x] * Th[x];
+          for (int x = tid; x < nc; x += PT) acc += double(Th[x]) * double(Th[x]);
           acc = pwarp_sum(acc);
           if (lane == 0) sh_red[warp] = acc;
           __syncthreads();
@@ -486,10 +504,10 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           for (int w = 0; w < PT / 32; ++w) nrm2 += sh_red[w];
           const double nrm = sqrt(nrm2);
           const bool ok = nrm > 0.0 && isfinite(nrm);
-          const double inv = ok ? 1.0 / nrm : 0.0;
+          const T inv = ok ? T(1.0 / nrm) : T(0);
           for (int64_t e = tid; e < site_vals; e += PT) {
             const int s = int(e / chi2), rem = int(e % chi2), a = rem / chi, b = rem % chi;
-            site_dst[e] = (a == 0 && b < kr) ? Th[s * kr + b] * inv : 0.0;
+            site_dst[e] = (a == 0 && b < kr) ? Th[s * kr + b] * inv : T(0);
           }
           if (tid == 0) {
             if (ok) sh_lam += log(nrm);
@@ -519,8 +537,8 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
         p_qr_pivot_rows(Th, Dl, nc, tau, sh_cn, sh_piv);
         for (int e = tid; e < Dl * rr; e += PT) {   // reflectors to Ap (column-major), R kept
           const int i = e / rr, j = e % rr;
-          double v = 0.0;
-          if (i > j) { v = Th[i * PLDT + j]; Th[i * PLDT + j] = 0.0; }
+          T v = T(0);
+          if (i > j) { v = Th[i * PLDT + j]; Th[i * PLDT + j] = T(0); }
           Ap[i + j * PM] = v;
         }
         for (int b = tid; b < nc; b += PT) sh_ipiv[sh_piv[b]] = b;
@@ -535,15 +553,15 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
         if (tid == 0) { const long long t1 = clock64(); sh_clk[2] += t1 - t_mark; t_mark = t1; }
         // singular values = row norms; keep the chi largest above cutoff x largest
         for (int i = tid; i < rr; i += PT) {
-          double s2 = 0.0;
+          T s2 = T(0);
           for (int x = 0; x < nc; ++x) s2 += Th[i * PLDT + x] * Th[i * PLDT + x];
           sn[i] = sqrt(s2);
         }
         __syncthreads();
         if (tid == 0) {
-          double mx = 0.0;
-          for (int i = 0; i < rr; ++i) mx = fmax(mx, sn[i]);
-          sh_smax = mx;
+          T mx = T(0);
+          for (int i = 0; i < rr; ++i) mx = sn[i] > mx ? sn[i] : mx;
+          sh_smax = double(mx);
         }
         __syncthreads();
         const double smax = sh_smax, thr = smax * lay.cutoff;
@@ -576,7 +594,7 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
         // cache site c: A[s][a''][j] = V^T[a''][(s, j)]
         for (int64_t e = tid; e < site_vals; e += PT) {
           const int s = int(e / chi2), rem = int(e % chi2), a = rem / chi, b = rem % chi;
-          double v = 0.0;
+          T v = T(0);
           if (a < kk && b < kr) {
             const int i = sh_src[a];
             v = Th[i * PLDT + sh_ipiv[s * kr + b]] / sn[i];   // column (s, b) sits at ipiv
@@ -584,7 +602,7 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           site_dst[e] = v;
         }
         // U S / s_max for site c - 1 (rows: the left bond of site c)
-        const double inv = smax > 0.0 ? 1.0 / smax : 0.0;
+        const T inv = smax > 0.0 ? T(1.0 / smax) : T(0);
         for (int e = tid; e < Dl * kk; e += PT) {
           const int p = e / kk, a = e % kk;
           const int i = sh_src[a];
@@ -600,23 +618,24 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
 }
 
 // log Z = lambda_0 + log sum over the top row's states (Eq. 6); one warp per realization.
+template <typename T>
 __global__ void potts_log_z_kernel(Layout lay, int q, double *logz) {
   const int n = blockIdx.x;
   const int lane = threadIdx.x;
   const RealInfo ri = lay.reals[n];
   const int L = ri.L, chi = lay.chi;
   const int64_t chi2 = int64_t(chi) * chi, site_vals = int64_t(q) * chi2;
-  const double *row0 = (const double *)lay.cache + ri.cache_off * site_vals;
+  const T *row0 = (const T *)lay.cache + ri.cache_off * site_vals;
   const int2 *b0 = lay.bonds + ri.bond_off;
   double v = lane == 0 ? 1.0 : 0.0, lacc = 0.0;
   for (int c = 0; c < L; ++c) {
     const int Dl = b0[c].x, Dr = b0[c + 1].x;
-    const double *A = row0 + int64_t(c) * site_vals;
+    const T *A = row0 + int64_t(c) * site_vals;
     double acc = 0.0;
     for (int a = 0; a < Dl; ++a) {
       const double va = __shfl_sync(0xffffffffu, v, a);
       if (lane < Dr)
-        for (int s = 0; s < q; ++s) acc += va * A[(int64_t(s) * chi + a) * chi + lane];
+        for (int s = 0; s < q; ++s) acc += va * double(A[(int64_t(s) * chi + a) * chi + lane]);
     }
     const double nrm = sqrt(pwarp_sum(acc * acc));
     v = nrm > 0.0 ? acc / nrm : 0.0;
@@ -633,12 +652,12 @@ constexpr int PS_CHAINS = 8;   // chains (warps) per sampler CTA
 
 // Proposals (FORCED = false) or teacher-forced scores (FORCED = true) of S chains per
 // realization; one warp per chain, lane b holds column b of the chain's vectors.
-template <bool FORCED>
+template <typename T, bool FORCED>
 __global__ void __launch_bounds__(32 * PS_CHAINS) potts_sample_kernel(
     Layout lay, int q, int S, uint64_t seed, uint64_t prop_base, const uint8_t *in_states,
     uint8_t *out_states, double *out_logq, double *out_E) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *As = (double *)smem_raw;   // q x chi x chi of the current site
+  T *As = (T *)smem_raw;   // q x chi x chi of the current site
   const int bpr = (S + PS_CHAINS - 1) / PS_CHAINS;
   const int n = blockIdx.x / bpr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -647,12 +666,12 @@ __global__ void __launch_bounds__(32 * PS_CHAINS) potts_sample_kernel(
   const RealInfo ri = lay.reals[n];
   const int L = ri.L, chi = lay.chi;
   const int64_t chi2 = int64_t(chi) * chi, site_vals = int64_t(q) * chi2;
-  const double *cache_n = (const double *)lay.cache + ri.cache_off * site_vals;
+  const T *cache_n = (const T *)lay.cache + ri.cache_off * site_vals;
   const int2 *bonds_n = lay.bonds + ri.bond_off;
   const float *jr = lay.jr + ri.site_off, *jd = lay.jd + ri.site_off;
   const int64_t L2 = int64_t(L) * L;
   const double beta = lay.beta;
-  double *rs = (double *)lay.samp_scratch + (ri.line_off * int64_t(lay.max_samples) + int64_t(act ? sid : 0) * L) * PCH;
+  T *rs = (T *)lay.samp_scratch + (ri.line_off * int64_t(lay.max_samples) + int64_t(act ? sid : 0) * L) * PCH;
   uint8_t *st = (FORCED ? nullptr : out_states + int64_t(S) * ri.site_off + int64_t(act ? sid : 0) * L2);
   const uint8_t *st_in = FORCED ? in_states + int64_t(S) * ri.site_off + int64_t(act ? sid : 0) * L2 : nullptr;
   auto state_at = [&](int i) -> int { return FORCED ? st_in[i] : st[i]; };
@@ -660,52 +679,52 @@ __global__ void __launch_bounds__(32 * PS_CHAINS) potts_sample_kernel(
   int64_t group = -1;
   U64x4 words{};
   bool bad = false;
-  auto stage = [&](const double *A) {
+  auto stage = [&](const T *A) {
     __syncthreads();
     for (int64_t e = threadIdx.x; e < site_vals; e += blockDim.x) As[e] = A[e];
     __syncthreads();
   };
   for (int r = 0; r < L; ++r) {
-    const double *row = cache_n + int64_t(r) * L * site_vals;
+    const T *row = cache_n + int64_t(r) * L * site_vals;
     const int2 *bd = bonds_n + int64_t(r) * (L + 1);
     // right pass: R_{L-1} = 1, R_c = T_{c+1}[s_up] R_{c+1}, normalised, spilled
-    double Rv = lane == 0 ? 1.0 : 0.0;
+    T Rv = lane == 0 ? T(1) : T(0);
     if (act && lane < PCH) rs[int64_t(L - 1) * PCH + lane] = Rv;
     for (int c = L - 2; c >= 0; --c) {
       stage(row + int64_t(c + 1) * site_vals);
       const int Dl = bd[c + 1].x, Dr = bd[c + 2].x;
-      double w[PQ];
+      T w[PQ];
       const int su = (r > 0 && act) ? state_at((r - 1) * L + c + 1) : 0;
 #pragma unroll
       for (int s = 0; s < PQ; ++s)
-        w[s] = (s < q && r > 0) ? pweight(beta, (double)jd[(r - 1) * L + c + 1], s == su) : (s < q ? 1.0 : 0.0);
-      double acc = 0.0;
+        w[s] = T((s < q && r > 0) ? pweight(beta, (double)jd[(r - 1) * L + c + 1], s == su) : (s < q ? 1.0 : 0.0));
+      T acc = T(0);
       for (int b = 0; b < Dr; ++b) {
-        const double rb = __shfl_sync(0xffffffffu, Rv, b);
+        const T rb = __shfl_sync(0xffffffffu, Rv, b);
         if (lane < Dl) {
-          double t = 0.0;
+          T t = T(0);
 #pragma unroll
           for (int s = 0; s < PQ; ++s)
             if (s < q) t += w[s] * As[(s * chi + lane) * chi + b];
           acc += t * rb;
         }
       }
-      const double nrm = sqrt(pwarp_sum(acc * acc));
-      Rv = nrm > 0.0 ? acc / nrm : 0.0;
-      if (act && lane < PCH) rs[int64_t(c) * PCH + lane] = lane < Dl ? Rv : 0.0;
+      const T nrm = sqrt(pwarp_sum(acc * acc));
+      Rv = nrm > T(0) ? acc / nrm : T(0);
+      if (act && lane < PCH) rs[int64_t(c) * PCH + lane] = lane < Dl ? Rv : T(0);
     }
     __syncwarp();
     // left sweep
-    double lv = lane == 0 ? 1.0 : 0.0;
+    T lv = lane == 0 ? T(1) : T(0);
     for (int c = 0; c < L; ++c) {
       stage(row + int64_t(c) * site_vals);
       const int Dl = bd[c].x, Dr = bd[c + 1].x;
-      const double Rc = (lane < Dr) ? rs[int64_t(c) * PCH + lane] : 0.0;
-      double v[PQ], rho[PQ];
+      const T Rc = (lane < Dr) ? rs[int64_t(c) * PCH + lane] : T(0);
+      T v[PQ], rho[PQ];
 #pragma unroll
-      for (int s = 0; s < PQ; ++s) v[s] = 0.0;
+      for (int s = 0; s < PQ; ++s) v[s] = T(0);
       for (int a = 0; a < Dl; ++a) {
-        const double la = __shfl_sync(0xffffffffu, lv, a);
+        const T la = __shfl_sync(0xffffffffu, lv, a);
         if (lane < Dr) {
 #pragma unroll
           for (int s = 0; s < PQ; ++s)
@@ -717,11 +736,11 @@ __global__ void __launch_bounds__(32 * PS_CHAINS) potts_sample_kernel(
       double tot = 0.0;
 #pragma unroll
       for (int s = 0; s < PQ; ++s) {
-        rho[s] = 0.0;
+        rho[s] = T(0);
         if (s < q) {
           rho[s] = fabs(pwarp_sum(v[s] * Rc));
-          if (r > 0) rho[s] *= pweight(beta, (double)jd[(r - 1) * L + c], s == su);
-          tot += rho[s];
+          if (r > 0) rho[s] *= T(pweight(beta, (double)jd[(r - 1) * L + c], s == su));
+          tot += double(rho[s]);
         }
       }
       int k;
@@ -740,25 +759,25 @@ __global__ void __launch_bounds__(32 * PS_CHAINS) potts_sample_kernel(
 #pragma unroll
         for (int s = 0; s < PQ - 1; ++s) {
           if (s < q - 1 && !found) {
-            cum += rho[s] / tot;
+            cum += double(rho[s]) / tot;
             if (u < cum) { k = s; found = true; }
           }
         }
       }
       if (!(tot > 0.0) || !isfinite(tot)) bad = true;
-      double rk = rho[0];
+      double rk = double(rho[0]);
 #pragma unroll
-      for (int s = 1; s < PQ; ++s) rk = (s == k) ? rho[s] : rk;
+      for (int s = 1; s < PQ; ++s) rk = (s == k) ? double(rho[s]) : rk;
       lq += log(rk / tot);
       if (c > 0) E -= (double)jr[r * L + c - 1] * (k == state_at(i - 1) ? 1.0 : 0.0);
       if (r > 0) E -= (double)jd[(r - 1) * L + c] * (k == su ? 1.0 : 0.0);
       if (!FORCED && act && lane == 0) st[i] = (uint8_t)k;
       __syncwarp();
-      double vk = v[0];
+      T vk = v[0];
 #pragma unroll
       for (int s = 1; s < PQ; ++s) vk = (s == k) ? v[s] : vk;
-      const double nrm = sqrt(pwarp_sum(vk * vk));
-      lv = nrm > 0.0 ? vk / nrm : 0.0;
+      const T nrm = sqrt(pwarp_sum(vk * vk));
+      lv = nrm > T(0) ? vk / nrm : T(0);
     }
   }
   if (act && lane == 0) {
@@ -770,36 +789,50 @@ __global__ void __launch_bounds__(32 * PS_CHAINS) potts_sample_kernel(
 
 }  // namespace
 
-int64_t potts_slot_bytes(int L_max) {
-  return align256(int64_t(L_max) * PM * PD * 8) + align256(int64_t(L_max) * 8);
+int64_t potts_slot_bytes(int L_max, int esz) {
+  return align256(int64_t(L_max) * PM * PD * esz) + align256(int64_t(L_max) * 8);
 }
 
-// q and chi limits of the float64 Potts kernels (panel sizes in shared memory)
+// q and chi limits of the Potts kernels (panel sizes in shared memory)
 bool potts_supported(int q, int chi) { return q >= 3 && q <= PQ && chi <= PCH && q * q * chi <= PM; }
 
 int potts_scratch_ch() { return PCH; }
 
-cudaError_t launch_potts_build(const Layout &lay, int q, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(potts_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       PottsSmem::bytes);
+template <typename T>
+static cudaError_t launch_potts_build_t(const Layout &lay, int q, cudaStream_t st) {
+  const int bytes = PottsSmem::n * int(sizeof(T));
+  cudaError_t e = cudaFuncSetAttribute(potts_build_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(lay.counter, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  potts_build_kernel<<<lay.env_slots, PT, PottsSmem::bytes, st>>>(lay, q);
+  potts_build_kernel<T><<<lay.env_slots, PT, bytes, st>>>(lay, q);
   return cudaGetLastError();
 }
 
-cudaError_t launch_potts_log_z(const Layout &lay, int q, double *logz, cudaStream_t st) {
-  potts_log_z_kernel<<<lay.n_real, 32, 0, st>>>(lay, q, logz);
+// prec: 0 = float64, 1 = float32 (build, cache and sampling contractions)
+cudaError_t launch_potts_build(const Layout &lay, int q, int prec, cudaStream_t st) {
+  return prec == 1 ? launch_potts_build_t<float>(lay, q, st) : launch_potts_build_t<double>(lay, q, st);
+}
+
+cudaError_t launch_potts_log_z(const Layout &lay, int q, int prec, double *logz, cudaStream_t st) {
+  if (prec == 1) potts_log_z_kernel<float><<<lay.n_real, 32, 0, st>>>(lay, q, logz);
+  else potts_log_z_kernel<double><<<lay.n_real, 32, 0, st>>>(lay, q, logz);
   return cudaGetLastError();
 }
 
-cudaError_t launch_potts_sample(const Layout &lay, int q, int S, uint64_t seed, uint64_t base,
-                                const uint8_t *in, uint8_t *out, double *lq, double *E, cudaStream_t st) {
+template <typename T>
+static void launch_potts_sample_t(const Layout &lay, int q, int S, uint64_t seed, uint64_t base,
+                                  const uint8_t *in, uint8_t *out, double *lq, double *E, cudaStream_t st) {
   const int bpr = (S + PS_CHAINS - 1) / PS_CHAINS;
-  const size_t smem = size_t(q) * lay.chi * lay.chi * 8;
-  if (in) potts_sample_kernel<true><<<lay.n_real * bpr, 32 * PS_CHAINS, smem, st>>>(lay, q, S, seed, base, in, out, lq, E);
-  else potts_sample_kernel<false><<<lay.n_real * bpr, 32 * PS_CHAINS, smem, st>>>(lay, q, S, seed, base, in, out, lq, E);
+  const size_t smem = size_t(q) * lay.chi * lay.chi * sizeof(T);
+  if (in) potts_sample_kernel<T, true><<<lay.n_real * bpr, 32 * PS_CHAINS, smem, st>>>(lay, q, S, seed, base, in, out, lq, E);
+  else potts_sample_kernel<T, false><<<lay.n_real * bpr, 32 * PS_CHAINS, smem, st>>>(lay, q, S, seed, base, in, out, lq, E);
+}
+
+cudaError_t launch_potts_sample(const Layout &lay, int q, int prec, int S, uint64_t seed, uint64_t base,
+                                const uint8_t *in, uint8_t *out, double *lq, double *E, cudaStream_t st) {
+  if (prec == 1) launch_potts_sample_t<float>(lay, q, S, seed, base, in, out, lq, E, st);
+  else launch_potts_sample_t<double>(lay, q, S, seed, base, in, out, lq, E, st);
   return cudaGetLastError();
 }
 
