@@ -81,3 +81,20 @@ def test_energies_exact_and_scores_reproduce_log_q(P, oracle_log_z, prec):
     assert np.array_equal(E2.cpu().numpy(), E)
     np.testing.assert_allclose(lq.cpu().numpy(), props.logq.cpu().numpy(), rtol=1e-12, atol=1e-12)
     assert np.all(props.logq.cpu().numpy() <= 0.0)
+
+
+@pytest.mark.parametrize("prec,bound", [("tf32", 1e-4), ("bf16", 2e-3)])
+def test_tensor_modes_at_chi64(P, prec, bound):
+    # the chi = 64 instantiation (the benchmark's) with the tensor-core products: L = 12, 13 at
+    # beta = 1, where chi = 64 is exact, against the oracle's log Z at the mode's cutoff
+    Ls, chi, beta = [12, 13], 64, 1.0
+    reals = parity.realizations(Ls, "pmj")
+    t = P.TNMC(Ls, chi, beta, prec, max_samples=8)
+    assert t.plan_ch == 64
+    t.build_envs(torch.from_numpy(parity.packed_J(reals)).cuda())
+    lz = t.log_z().cpu().numpy()
+    torch.cuda.synchronize()
+    assert t.device_status()[0] == 0
+    envs = parity.oracle_envs(reals, beta, chi, t.cutoff)
+    for n, L in enumerate(Ls):
+        assert abs(lz[n] - bmps.log_z(envs[n])) / (L * L) <= bound, (n, lz[n], bmps.log_z(envs[n]))
