@@ -132,3 +132,31 @@ def test_draw_rule_is_the_first_partial_sum_above_u():
     u = philox.spin_uniforms(1, np.arange(S, dtype=np.uint64), 0, 9)[:, 0]
     assert np.array_equal(st[:, 0, 0], np.floor(u * q).astype(np.uint8))
     np.testing.assert_allclose(lq, -np.log(q), atol=1e-15)
+
+
+def test_mh_with_a_poor_potts_proposal_samples_boltzmann():
+    """A chi = 1 Potts proposal (far from P), corrected by Eq. 10 with the Potts energy, samples
+    P: chi-squared of the chain's states over the 81 states of an L = 2, q = 3 lattice."""
+    from oracle import mh
+    L, q, beta, S = 2, 3, 0.8, 60000
+    Jh, Jv = draw_bonds(L, 1023, "pmj")
+    rows = potts.build_envs(Jh, Jv, beta, q, 1)
+    props = potts.propose(rows, Jh, Jv, beta, q, S, 11, 0, 0)[:3]
+    start = (np.zeros((L, L), np.uint8), np.inf, 0.0)     # an empty chain: the first proposal is taken
+    _, acc, _, _ = mh.chain(start, props, beta, 11, 0, 0)
+    assert acc[0] == 1 and 0.05 < acc.mean() < 0.99
+    codes = props[0].reshape(S, -1).astype(np.int64) @ (q ** np.arange(L * L - 1, -1, -1))
+    states = np.empty(S, np.int64)
+    cur = codes[0]
+    for k in range(S):
+        if acc[k]:
+            cur = codes[k]
+        states[k] = cur
+    cnt = np.bincount(states, minlength=q ** (L * L))
+    _, _, logp, _ = potts.brute_force(Jh, Jv, beta, q)
+    exp_cnt = S * np.exp(logp)
+    keep = exp_cnt > 10
+    tau = 1.0 / acc.mean()          # successive states are correlated
+    chi2 = float(((cnt[keep] - exp_cnt[keep]) ** 2 / exp_cnt[keep]).sum()) / tau
+    dof = int(keep.sum()) - 1
+    assert chi2 < dof + 6 * np.sqrt(2 * dof), (chi2, dof)
