@@ -1,11 +1,13 @@
 """Checkpointed environments (every K-th row cached, segments rebuilt before sampling)
-give the same bits as the fully cached environments, through the C ABI."""
+give the same bits as the fully cached environments, through the C ABI, and meet the
+oracle directly (Sec. 3.5: environments recomputed per segment)."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import bmps  # noqa: E402
 import parity  # noqa: E402
 
 
@@ -83,3 +85,29 @@ def test_cluster_wait_that_runs_out_reports_timeout(P):
     st, flags = t.device_status()
     assert st == 0 and not flags.any()
     np.testing.assert_allclose(lz, lz_ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("prec,K", [("fp64", 3), ("dfloat", 4)])
+def test_checkpointed_handle_meets_the_oracle(P, prec, K):
+    # direct parity of a checkpointed handle (not only through the full cache): log Z and the
+    # free-running proposals, whose rows come from segments rebuilt from their checkpoints
+    Ls, chi, beta, S = [13, 10], 8, 1.2, 48
+    reals = parity.realizations(Ls, "pmj")
+    t = P.TNMC(Ls, chi, beta, prec, max_samples=S, ckpt_every=K)
+    t.build_envs(torch.from_numpy(parity.packed_J(reals)).cuda())
+    lz = t.log_z().cpu().numpy()
+    props = t.propose(S, 42, 0)
+    torch.cuda.synchronize()
+    st, flags = t.device_status()
+    assert st == 0 and not flags.any()
+    envs = parity.oracle_envs(reals, beta, chi, t.cutoff)
+    spins = parity.split_spins(props.spins.cpu().numpy(), Ls, S)
+    rel, band, lq_atol = (1e-10, 1e-9, 1e-9) if prec == "fp64" else (1e-9, 1e-7, 1e-8)
+    bd = 0
+    for n, ((Jh, Jv), rows) in enumerate(zip(reals, envs)):
+        o = bmps.log_z(rows)
+        assert abs(lz[n] - o) < rel * abs(o), (n, lz[n], o)
+        _, nb = parity.compare_proposals(rows, Jh, Jv, beta, 42, 0, n, spins[n], props.logq.cpu().numpy()[n],
+                                         props.E.cpu().numpy()[n], band=band, lq_atol=lq_atol)
+        bd += nb
+    assert bd <= 2
