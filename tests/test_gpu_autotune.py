@@ -17,6 +17,9 @@ import parity  # noqa: E402
 
 CANDIDATES = [0, 1, 2, 4, 12]
 CANDIDATES_FP32 = [0, 8, 16, 17, 18, 32, 40]   # one CTA (4 or 8 lanes), pairs (bit 4), QR preconditioning (bit 5)
+# valid layouts the autotuner does not time: preconditioned CTA pairs (bits 4 and 5; won 6 middle
+# rows of the L = 256 float32 workload by 2.5 % but lost the full build by 11 %)
+LAYOUTS_FP32 = CANDIDATES_FP32 + [48, 49, 50]
 
 
 @pytest.fixture(scope="module")
@@ -54,7 +57,7 @@ def test_every_layout_matches_the_oracle(P, prec, variant):
         assert nbd <= 1
 
 
-@pytest.mark.parametrize("variant", CANDIDATES_FP32)
+@pytest.mark.parametrize("variant", LAYOUTS_FP32)
 def test_every_float32_layout_matches_the_oracle(P, variant):
     # float32: |d log Z| / L^2 <= 1e-6 (where cut gaps are wide, beta = 1) and every draw the
     # oracle's outside the float32 band; the pair layouts move sector 1's Jacobi to a second SM,
