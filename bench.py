@@ -344,7 +344,7 @@ def run_arm(P, gw, ids, args, prec, steps, dev):
     _, _, rowinfo = t.set_diagnostics(rowinfo=True)
     state = t.mh_init_empty()
     stream = t.stream
-    step_ms, env_ms, accepted, decided = [], [], 0, 0
+    step_ms, env_ms, accepted, decided, by_step = [], [], 0, 0, []
     for k in range(steps):
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
@@ -361,10 +361,12 @@ def run_arm(P, gw, ids, args, prec, steps, dev):
         a = int(acc.sum().item())
         if k == 0:
             a -= n                      # the forced first acceptance of every chain
-            decided += n * (S - 1)
+            d = n * (S - 1)
         else:
-            decided += n * S
+            d = n * S
         accepted += a
+        decided += d
+        by_step.append(a / d)
         step_ms.append(e0.elapsed_time(e2))
         env_ms.append(e0.elapsed_time(e1))
         if k == 0:
@@ -375,6 +377,7 @@ def run_arm(P, gw, ids, args, prec, steps, dev):
     acceptance = accepted / decided
     out = {"precision": prec, "steps": steps, "step_s": step_s,
            "env_build_s": sum(env_ms) / len(env_ms) / 1e3, "acceptance": acceptance,
+           "acceptance_by_step": by_step,   # step k: the same proposal ids and seed in every arm
            "accepted_per_s": acceptance * n * S / step_s, "proposals_per_s": n * S / step_s,
            "cutoff": t.cutoff, "bond_dim_mean": dmean, "device_status": int(st),
            "build_variant": t.build_variant, "autotune_ms": tune}

@@ -299,9 +299,10 @@ __device__ void householder_qr_strided(T *A, int m, int n, T *tau, int half, int
     const T tj = tau[j];
     if (tj != T(0) || PIVOT) {   // pivoting refreshes the column norms even for a null reflector
       const T *v = A + int64_t(j) * CS;
-      if constexpr (std::is_same<T, dfloat>::value || PIVOT) {
-        // double-float (and pivoting): 8 lanes per column (32 columns at a time), 3-level
-        // reductions
+      if constexpr (!std::is_same<T, double>::value || PIVOT) {
+        // float32, double-float (and pivoting): 8 lanes per column (32 columns at a time),
+        // 3-level reductions; at the float32 build's bonds a warp per column leaves most
+        // lanes idle and pays 5 shuffle levels per column
         // (the trip count is uniform over the half: every lane reaches the shuffles)
         constexpr int G = 8;
         const int grp = ht / G, gl = ht % G;
@@ -484,7 +485,27 @@ __device__ void form_q_2b(T *A, const T *tau, int m, int kq, int half, int ht) {
   const int hw = ht >> 5, lane = ht & 31;
   for (int j = kq - 1; j >= 0; --j) {
     const T tj = tau[j];
-    if (tj != T(0)) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (tj != T(0)) {
+      // float32: 8 lanes per column, 32 columns at a time (uniform trip count over the half)
+      constexpr int G = 8;
+      const int grp = ht / G, gl = ht % G;
+      const T *v = A + int64_t(j) * LDA;
+      for (int l0 = j + 1; l0 < kq; l0 += 256 / G) {
+        const int l = l0 + grp;
+        const bool on = l < kq;
+        T *ql = A + int64_t(on ? l : j) * LDA;
+        T w = (on && gl == 0) ? ql[j] : T(0);
+        if (on)
+          for (int i = j + 1 + gl; i < m; i += G) dacc(w, v[i], ql[i]);
+        w = group_sum<T, G>(dfin(w)) * tj;
+        if (on) {
+          if (gl == 0) ql[j] -= w;
+          for (int i = j + 1 + gl; i < m; i += G) ql[i] = axmy(ql[i], w, v[i]);
+        }
+      }
+      }
+    } else if (tj != T(0)) {
       const T *v = A + int64_t(j) * LDA;
       for (int l = j + 1 + hw; l < kq; l += 8) {
         T *ql = A + int64_t(l) * LDA;
@@ -1010,7 +1031,7 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
   __shared__ long long sh_key[2 * CH];   // ordering keys of the singular values
   __shared__ TC Bnrm[2 * CH];        // squared row norms cached by the Jacobi sweeps
   __shared__ TC sh_scl[4 * CH];      // Jacobi row scales (d, 1/d) of float64 rows, per sector
-  __shared__ TC sh_tv, sh_th, sh_smax;
+  __shared__ TC sh_tv, sh_th, sh_smax, sh_rscale;
   __shared__ long long sh_clk[5];    // cycles per phase of the current row (diagnostics)
   // cluster mode: task (rank 1 reads) and result (rank 0 reads) mailboxes
   __shared__ unsigned sh_task_seq, sh_done_seq, sh_sent;
@@ -1228,15 +1249,18 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         householder_qr<TC, LDA>(Aq, m, Dn, tau + half * CH, half, ht);
         __syncthreads();
         const int kq = min(m, Dn);
-        if (tid == 0) {
+        if (tid == 0 && lay.dbg_rowinfo) {   // the row records' flop count
           const double mm = m, nn = kq;
           sh_flops += 2.0 * (2.0 * (2.0 * mm * nn * nn - 2.0 * nn * nn * nn / 3.0))  // QR + Q, 2 sectors
                       + 2.0 * mm * Dn * Dc;                                          // MPO x MPS product
         }
         // R = upper trapezoid; both sectors normalised together
         {
-          // squared norm: double-float rows sum in double-float (no float64 per element)
-          using TA = typename std::conditional<std::is_same<TC, dfloat>::value, dfloat, double>::type;
+          // squared norm: double-float rows sum in double-float, float32 rows in float32 (the
+          // norm only picks a scale; log Z adds the log of the float32 scale applied), float64
+          // rows in float64. The scalar chain (sum over warps, root, reciprocal, log) runs on
+          // one thread: run by all 16 warps it queued 16 copies on the slow float64 pipe
+          using TA = typename std::conditional<std::is_same<TC, double>::value, double, TC>::type;
           TA acc = TA(0.0);
           for (int e = tid; e < 2 * kq * Dn; e += ENV_THREADS) {
             const int q = e / (kq * Dn), rem = e % (kq * Dn), i = rem / Dn, b = rem % Dn;
@@ -1245,15 +1269,19 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
           acc = warp_sum(acc);
           if (lane == 0) sh_red[warp] = double(acc);
           __syncthreads();
-          double nrm2 = 0.0;
-          for (int w = 0; w < ENV_THREADS / 32; ++w) nrm2 += sh_red[w];
-          const double nrm = sqrt(nrm2);
-          const bool ok = nrm > 0.0 && isfinite(nrm);
           if (tid == 0) {
-            if (ok) sh_lam += log(nrm);
-            else set_flag(lay.flags, n, FLAG_NUMERIC);
+            double nrm2 = 0.0;
+            for (int w = 0; w < ENV_THREADS / 32; ++w) nrm2 += sh_red[w];
+            const double nrm = sqrt(nrm2);
+            const bool ok = nrm > 0.0 && isfinite(nrm);
+            const TC sc = ok ? TC(1.0 / nrm) : TC(0);
+            if (!ok) set_flag(lay.flags, n, FLAG_NUMERIC);
+            else if constexpr (std::is_same<TC, float>::value) sh_lam -= log(double(sc));
+            else sh_lam += log(nrm);
+            sh_rscale = sc;
           }
-          const TC inv = ok ? TC(1.0 / nrm) : TC(0);
+          __syncthreads();
+          const TC inv = sh_rscale;
           for (int e = tid; e < 2 * kq * Dn; e += ENV_THREADS) {
             const int q = e / (kq * Dn), rem = e % (kq * Dn), i = rem / Dn, b = rem % Dn;
             Rb[q * P::CH2 + int64_t(i) * CH + b] =
@@ -1522,48 +1550,61 @@ __global__ void __launch_bounds__(ENV_THREADS, 1) env_build_kernel(Layout lay) {
         }
         __syncthreads();
         if (warp == 0) {
-          // kept counts per sector, the cut gap and the discarded weight, over warp 0
+          // kept counts per sector over warp 0; for the row records also the cut gap and the
+          // discarded weight (float64 work kept off the build unless asked for)
+          const bool stats = lay.dbg_rowinfo != nullptr;
           int ne = 0, no = 0;
           double kept_min = 1e300, drop_max = 0.0, tot = 0.0, drop = 0.0;
           for (int i = lane; i < m; i += 32) {
-            const double s = (double)sn[i];
-            tot += s * s;
-            if (sh_keep[i] >= 0) {
-              if (i < k0) ++ne; else ++no;
-              kept_min = s < kept_min ? s : kept_min;
-            } else {
-              drop += s * s;
-              drop_max = s > drop_max ? s : drop_max;
+            const bool kept = sh_keep[i] >= 0;
+            if (kept) { if (i < k0) ++ne; else ++no; }
+            if (stats) {
+              const double s = (double)sn[i];
+              tot += s * s;
+              if (kept) {
+                kept_min = s < kept_min ? s : kept_min;
+              } else {
+                drop += s * s;
+                drop_max = s > drop_max ? s : drop_max;
+              }
             }
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
             ne += __shfl_xor_sync(0xffffffffu, ne, o);
             no += __shfl_xor_sync(0xffffffffu, no, o);
-            tot += __shfl_xor_sync(0xffffffffu, tot, o);
-            drop += __shfl_xor_sync(0xffffffffu, drop, o);
-            const double km = __shfl_xor_sync(0xffffffffu, kept_min, o);
-            const double dm = __shfl_xor_sync(0xffffffffu, drop_max, o);
-            kept_min = km < kept_min ? km : kept_min;
-            drop_max = dm > drop_max ? dm : drop_max;
+          }
+          if (stats) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              tot += __shfl_xor_sync(0xffffffffu, tot, o);
+              drop += __shfl_xor_sync(0xffffffffu, drop, o);
+              const double km = __shfl_xor_sync(0xffffffffu, kept_min, o);
+              const double dm = __shfl_xor_sync(0xffffffffu, drop_max, o);
+              kept_min = km < kept_min ? km : kept_min;
+              drop_max = dm > drop_max ? dm : drop_max;
+            }
           }
           if (lane == 0) {
             sh_newE = ne; sh_newO = no;
-            sh_dmax = max(sh_dmax, ne + no);
-            sh_dsum += ne + no;
-            if (drop_max > 0.0) {
-              const double gap = kept_min / drop_max - 1.0;
-              sh_gap = gap < sh_gap ? gap : sh_gap;
-              sh_ntr += 1;
+            if (stats) {
+              sh_dmax = max(sh_dmax, ne + no);
+              sh_dsum += ne + no;
+              if (drop_max > 0.0) {
+                const double gap = kept_min / drop_max - 1.0;
+                sh_gap = gap < sh_gap ? gap : sh_gap;
+                sh_ntr += 1;
+              }
+              if (tot > 0.0) { const double d = drop / tot; sh_disc = d > sh_disc ? d : sh_disc; }
             }
-            if (tot > 0.0) { const double d = drop / tot; sh_disc = d > sh_disc ? d : sh_disc; }
-            if (smax > TC(0) && isfinite((double)smax)) sh_lam += log((double)smax);
-            else set_flag(lay.flags, n, FLAG_NUMERIC);
           }
+        } else if (tid == 32) {   // the log scale of this site, beside warp 0's counts
+          if (smax > TC(0) && isfinite((double)smax)) sh_lam += log((double)smax);
+          else set_flag(lay.flags, n, FLAG_NUMERIC);
         }
         __syncthreads();
         const int ne = sh_newE, no = sh_newO, nk = ne + no;
-        if (tid == ENV_THREADS - 32) {   // the flop count, off warp 0
+        if (tid == ENV_THREADS - 32 && lay.dbg_rowinfo) {   // the row records' flop count, off warp 0
           for (int q = 0; q < 2; ++q) {
             const double rq = q ? k1 : k0;
             const double a = rq > N ? rq : N, b = rq > N ? N : rq;

@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
   __shared__ T sh_cn[PD];     // column norms of the pivoted QR
   __shared__ int sh_piv[PD], sh_ipiv[PD];
   __shared__ double sh_lam, sh_smax, sh_flops, sh_dsum;
+  __shared__ T sh_rscale;
   __shared__ int sh_n, sh_flag, sh_keep, sh_kprev, sh_sweeps, sh_svds;
   __shared__ long long sh_clk[4];   // cycles of the row: phase A, Theta products, Jacobi, selection + stores
   long long t_mark = 0;
@@ -438,18 +439,20 @@ __global__ void __launch_bounds__(PT, 1) potts_build_kernel(Layout lay, int q) {
           acc = pwarp_sum(acc);
           if (lane == 0) sh_red[warp] = acc;
           __syncthreads();
-          double nrm2 = 0.0;
-          for (int w = 0; w < PT / 32; ++w) nrm2 += sh_red[w];
-          const double nrm = sqrt(nrm2);
-          const bool ok = nrm > 0.0 && isfinite(nrm);
-          const T inv = ok ? T(1.0 / nrm) : T(0);
+          if (tid == 0) {   // the scalar chain on one thread (not 16 warps on the float64 pipe)
+            double nrm2 = 0.0;
+            for (int w = 0; w < PT / 32; ++w) nrm2 += sh_red[w];
+            const double nrm = sqrt(nrm2);
+            const bool ok = nrm > 0.0 && isfinite(nrm);
+            sh_rscale = ok ? T(1.0 / nrm) : T(0);
+            if (ok) sh_lam += log(nrm);
+            else set_flag(lay.flags, n, FLAG_NUMERIC);
+          }
+          __syncthreads();
+          const T inv = sh_rscale;
           for (int e = tid; e < kq * ncol; e += PT) {
             const int i = e / ncol, b = e % ncol;
             Rb[i * PD + b] = (b >= i) ? Ap[i + b * PM] * inv : T(0);
-          }
-          if (tid == 0) {
-            if (ok) sh_lam += log(nrm);
-            else set_flag(lay.flags, n, FLAG_NUMERIC);
           }
         }
         __syncthreads();
