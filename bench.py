@@ -565,10 +565,10 @@ def run_ours(args, wl):
         proposals = n_mine * S * args.steps
         # DRAM bytes per launch of the float32, chi = 64 build in its preconditioned 8-lane
         # layout (variant 40): an ncu capture of 8 realizations at L = 128 (131072 site-rows)
-        # read + wrote 2.181 GB; traffic grows with the site-rows written
+        # read + wrote 2.178 GB; traffic grows with the site-rows written
         site_rows = sum(L * L for L in my_Ls)
         if args.prec == "fp32" and plan_ch == 64 and not ckpt and variant_primary == 40:
-            traffic = 2.181e9 / 131072 * site_rows
+            traffic = 2.178e9 / 131072 * site_rows
             traffic_src = "ncu capture at L=128 x 8 realizations (layout 40), scaled by site-rows"
         else:
             traffic, traffic_src = None, "no capture of this instantiation"
