@@ -6,7 +6,7 @@ realization with log q and energies, and the independence Metropolis-Hastings
 scan (Sec. 3.2-3.4, Eq. 10). Default workload: 64 +-J realizations at L = 256,
 beta = 3, chi = 64, S = 256 (the accepted-samples/s workload).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|fp32|mixed]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|fp32|mixed|dfloat|tf32|bf16]
                     [--impl ours|reference] [--workload L256|gauss128|L1024|...]
                     [--learned [--teacher-chi 32] [--train-steps 4000]] [--ckpt K]
 
@@ -409,7 +409,14 @@ def run_ours(args, wl):
     Jhost = torch.from_numpy(gw.packed_J(ids)).pin_memory()
     J = Jhost.to(dev)
     S = wl.S
-    ckpt = args.ckpt if args.ckpt >= 0 else (32 if max(wl.Ls) >= 1024 else 0)
+    if args.ckpt >= 0:
+        ckpt = args.ckpt
+    else:
+        # checkpoints only where the full cache does not fit: its workspace against 60 % of the
+        # device's free memory (the proposals, at L = 1024 17 GB of spins, need room beside it)
+        full = P.workspace_size(my_Ls, wl.chi, wl.beta, P.PRECISIONS[args.prec], S,
+                                cutoff=args.cutoff, q=wl.q)
+        ckpt = 0 if full <= 0.6 * torch.cuda.mem_get_info(dev)[0] else 32
     t = P.TNMC(my_Ls, wl.chi, wl.beta, args.prec, max_samples=S, device=dev, cutoff=args.cutoff,
                ckpt_every=ckpt, q=wl.q)
     t.set_realization_ids(ids)
@@ -870,7 +877,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3,
                     help="steps of the end-to-end leg (host buffers), at most --steps")
     ap.add_argument("--ckpt", type=int, default=-1,
-                    help="cache every K-th environment row (default: 32 for L >= 1024, else off)")
+                    help="cache every K-th environment row (default: 32 where the full cache "
+                         "does not fit in 60 %% of the free device memory, else off)")
     ap.add_argument("--learned", action="store_true",
                     help="train the learned correction (setup) and time the corrected steps")
     ap.add_argument("--teacher-chi", type=int, default=32)
