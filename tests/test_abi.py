@@ -54,11 +54,26 @@ def test_workspace_size_host_only(P):
     ([16], 4, float("nan"), 1, 4),
     ([16], 4, 1.0, 9, 4),        # unknown precision
     ([16], 4, 1.0, 1, 0),        # max_samples < 1
+    ([], 4, 1.0, 1, 4),          # no realization
+    ([16], 4, 1.0, 1, 4, 1.0),   # cutoff >= 1 keeps nothing
+    ([16], 4, 1.0, 1, 4, 0.0, 1),        # a checkpoint every row is the full cache
+    ([16], 4, 1.0, 1, 4, 0.0, 0, 1),     # one state per site
 ])
 def test_argument_checks(P, args):
     with pytest.raises(P.TnmcError) as e:
         P.workspace_size(*args)
     assert e.value.status == 1
+
+
+def test_potts_requests_beyond_the_kernels_are_unsupported(P):
+    for args in (([16], 4, 1.0, P.TNMC_DFLOAT, 4, 0.0, 0, 3),    # double-float Potts
+                 ([16], 4, 1.0, P.TNMC_FP64, 4, 0.0, 4, 3),      # checkpoints
+                 ([16], 32, 1.0, P.TNMC_FP64, 4, 0.0, 0, 3),     # chi above the panels
+                 ([16], 4, 1.0, P.TNMC_FP64, 4, 0.0, 0, 5)):     # q above the panels
+        with pytest.raises(P.TnmcError) as e:
+            P.workspace_size(*args)
+        assert e.value.status == 7, args
+    assert P.workspace_size([16], 16, 1.0, P.TNMC_FP32, 4, 0.0, 0, 3) > 0
 
 
 def test_tensor_core_precisions_size_like_float32(P):

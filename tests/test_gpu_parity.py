@@ -86,6 +86,25 @@ def test_fp64_log_z_spectra_and_proposals(P, Ls, chi, beta, kind):
     assert total_bd <= 1
 
 
+@pytest.mark.parametrize("prec", ["fp64", "dfloat"])
+def test_single_chain_at_a_far_proposal_base(P, prec):
+    # S = 1: one chain in a CTA laid out for 64, and a proposal id far from 0 (the Philox
+    # counter of the draw, Sec. 3.3); the oracle draws the same proposal from its own stream
+    Ls, chi, beta, base = [7, 5, 1], 8, 1.1, 123_456_789
+    t, reals, lz, props, _, st, flags = _run(P, Ls, chi, beta, prec, "pmj", 1, prop_base=base)
+    assert st == 0 and not flags.any()
+    envs = parity.oracle_envs(reals, beta, chi)
+    spins = parity.split_spins(props.spins.cpu().numpy(), Ls, 1)
+    lq, E = props.logq.cpu().numpy(), props.E.cpu().numpy()
+    band, atol = (parity.BAND_FP64, 1e-9) if prec == "fp64" else (1e-7, 1e-8)
+    n_bd = 0
+    for n, ((Jh, Jv), rows) in enumerate(zip(reals, envs)):
+        assert abs(lz[n] - bmps.log_z(rows)) < 1e-9 * max(1.0, abs(lz[n]))
+        n_bd += parity.compare_proposals(rows, Jh, Jv, beta, 42, base, n, spins[n], lq[n], E[n],
+                                         band=band, lq_atol=atol)[1]
+    assert n_bd == 0
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_score_matches_propose(P, prec):
     Ls, chi, beta = [9, 6], 4, 1.3
