@@ -143,6 +143,13 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def workload_config(wl, world: int) -> dict:
+    """The workload keys of the line's `config` object, the same in both arms' lines."""
+    return {"workload": wl.name, "L": wl.Ls[0], "chi": wl.chi, "beta": wl.beta,
+            "realizations_per_gpu": wl.n_real, "realizations": world * wl.n_real,
+            "samples_per_realization": wl.S, "q_states": wl.q}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -260,7 +267,7 @@ def run_reference(args, wl):
     line = {"impl": "reference", "metric": metric_name(wl), "value": v, "unit": "accepted/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl.name, "realizations": 1},
+            "data": "synthetic", "config": workload_config(wl, world),
             "cpu_baseline": {"value": v, "unit": "accepted/s", "cores": cpu_cores(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "accepted/s", "h2d_bytes_per_step": 0,
@@ -609,9 +616,7 @@ def run_ours(args, wl):
             "data": ("synthetic Gaussian N(0,1) disorder, seeded" if wl.kind == "gauss"
                      else "synthetic +-J disorder (p = 1/2), seeded")
                     + (f", {wl.q}-state Potts" if wl.q > 2 else ""),
-            "config": {"workload": wl.name, "L": wl.Ls[0], "chi": wl.chi, "beta": wl.beta,
-                       "realizations_per_gpu": wl.n_real, "realizations": n_all, "samples_per_realization": S,
-                       "q_states": wl.q,
+            "config": {**workload_config(wl, world),
                        "precision": args.prec, "cutoff": cutoff_primary, "ckpt_every": ckpt,
                        "build_variant": variant_primary, "autotune_ms": tune,
                        "learned_correction": bool(args.learned),
