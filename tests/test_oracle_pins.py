@@ -37,6 +37,40 @@ def test_philox_matches_numpy_bit_generator():
     np.testing.assert_array_equal(got, ref)
 
 
+def _numpy_philox_block(ctr, key):
+    """The Philox4x64-10 block of a 256-bit counter from numpy.random.Philox, which
+    increments its state counter (with carry) before producing a block."""
+    v = sum(int(x) << (64 * k) for k, x in enumerate(ctr))
+    v = (v - 1) % (1 << 256)
+    prev = np.array([(v >> (64 * k)) & (2 ** 64 - 1) for k in range(4)], np.uint64)
+    return np.random.Philox(counter=prev, key=np.array(key, np.uint64)).random_raw(4)
+
+
+def _uniform_of(w):
+    return (2 * (int(w) >> 12) + 1) * 2.0 ** -53       # exact in float64
+
+
+def test_draw_counters_follow_the_published_layout():
+    """The three streams against numpy's Philox on the counters the C ABI publishes: site i
+    of proposal t in realization g, key (seed, 0): spin draw (i >> 2, t, g, 0) word i & 3;
+    accept test (0, t, g, 1) word 0; random initial state (i >> 2, 0, g, 2) word i & 3,
+    its top bit. Proposal ids from 0 to 2^40 + 3."""
+    seed, g, L = 42, 5, 6
+    ts = np.array([0, 1, 7, 123_456_789, 2 ** 40 + 3], np.uint64)
+    u = philox.spin_uniforms(L, ts, g, seed)
+    for a, t in enumerate(ts):
+        for i in (0, 1, 3, 4, 17, L * L - 1):
+            w = _numpy_philox_block([i >> 2, t, g, 0], (seed, 0))[i & 3]
+            assert u[a, i] == _uniform_of(w), (t, i)
+    um = philox.mh_uniforms(ts, g, seed)
+    for a, t in enumerate(ts):
+        assert um[a] == _uniform_of(_numpy_philox_block([0, t, g, 1], (seed, 0))[0]), t
+    s = philox.init_spins(L, g, seed).reshape(-1)
+    for i in range(L * L):
+        w = _numpy_philox_block([i >> 2, 0, g, 2], (seed, 0))[i & 3]
+        assert s[i] == int(w) >> 63, i
+
+
 def test_uniform_map_open_interval_and_exact():
     w = np.array([0, 2 ** 64 - 1, 2 ** 63, 4095, 4096], dtype=np.uint64)
     u = philox.to_uniform(w)
