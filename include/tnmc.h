@@ -129,17 +129,20 @@ typedef struct {
 
 typedef struct tnmc_handle tnmc_handle;
 
-/* Human-readable name of a status code (static string, never NULL). */
+/* Human-readable name of a status code (static string, never NULL; unknown codes
+ * get a generic name). The paper has no counterpart. Cannot fail. */
 const char *tnmc_status_string(tnmc_status s);
 
-/* Bytes of device workspace a configuration needs (written to *bytes).
- * The size covers the coupling copy, the environment cache (L_n^2 sites of
- * chi x chi values per realization), the per-row log scales and bond sector
- * sizes, and the scratch of the environment build and of the sampler
- * (right environments of max_samples chains). Errors: TNMC_ERR_ARG. */
+/* Bytes of device workspace a configuration needs (written to *bytes); host only.
+ * The size covers the coupling copy, the environment cache (Sec. 3.2 keeps one
+ * environment per row; here L_n^2 sites of chi x chi values per realization, held in
+ * device memory rather than on disk), the per-row log scales and bond sector sizes, and
+ * the scratch of the environment build and of the sampler (right environments of
+ * max_samples chains). Errors: TNMC_ERR_ARG (a field out of range or a NULL argument),
+ * TNMC_ERR_UNSUPPORTED (a Potts request beyond the kernels, see q_states). */
 tnmc_status tnmc_workspace_size(const tnmc_config *cfg, size_t *bytes);
 
-/* Bind a configuration to a workspace and a CUDA stream.
+/* Bind a configuration to a workspace and a CUDA stream (the paper has no counterpart).
  * d_ws: device pointer, 256-byte aligned, at least tnmc_workspace_size bytes;
  *       owned by the caller and used by the handle until tnmc_destroy.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
@@ -148,7 +151,8 @@ tnmc_status tnmc_workspace_size(const tnmc_config *cfg, size_t *bytes);
 tnmc_status tnmc_create(const tnmc_config *cfg, void *d_ws, size_t ws_bytes,
                         void *cuda_stream, tnmc_handle **out);
 
-/* Release the host handle (the workspace stays the caller's). NULL is a no-op. */
+/* Release the host handle (the workspace stays the caller's). NULL is a no-op. The
+ * paper has no counterpart. Cannot fail. */
 void tnmc_destroy(tnmc_handle *h);
 
 /* Build the boundary-MPS environments of every realization (Sec. 3.2 and
@@ -179,14 +183,20 @@ tnmc_status tnmc_log_z(tnmc_handle *h, double *d_logz);
 tnmc_status tnmc_propose(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop_base,
                          uint8_t *d_spins, double *d_logq, double *d_E);
 
-/* Teacher-forced scoring: log q and E of S given configurations per
- * realization (same layouts as tnmc_propose; d_spins is read-only here). */
+/* Teacher-forced scoring (Sec. 3.3 with every spin forced; Eq. 9 and Eq. 1): log q and E
+ * of S given configurations per realization (same layouts as tnmc_propose; d_spins is
+ * read-only here). A configuration with a vanished conditional scores log q = -inf.
+ * Errors: TNMC_ERR_ARG (S < 1 or S > max_samples, a NULL pointer), TNMC_ERR_STATE
+ * (before tnmc_build_envs), TNMC_ERR_CUDA. */
 tnmc_status tnmc_score(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
                        double *d_logq, double *d_E);
 
 /* Random initial chain state of every realization (uniform spins, Philox
- * stream 2, proposal id 0) scored by the proposal q.
- * d_state_spins: uint8 [sum L_n^2]; d_state_logq, d_state_E: float64 [n_real]. */
+ * stream 2, proposal id 0) scored by the proposal q: the start of the independence chain
+ * of Eq. 10 (the paper does not state its chains' start).
+ * d_state_spins: uint8 [sum L_n^2]; d_state_logq, d_state_E: float64 [n_real].
+ * Errors: TNMC_ERR_ARG, TNMC_ERR_STATE (before tnmc_build_envs), TNMC_ERR_CUDA,
+ * TNMC_ERR_UNSUPPORTED (Potts handles: use tnmc_mh_init_empty). */
 tnmc_status tnmc_mh_init(tnmc_handle *h, uint64_t seed, uint8_t *d_state_spins,
                          double *d_state_logq, double *d_state_E);
 
@@ -205,11 +215,12 @@ tnmc_status tnmc_observables(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
 
 /* A chain state with no configuration yet: spins 0, E = 0 and log q = +inf,
  * so that the first proposal of the next tnmc_mh_step has log r = +inf and is
- * accepted: the chain then starts at a draw of q (the paper has no
- * counterpart). Use it where the random state of tnmc_mh_init can have
+ * accepted: the chain then starts at a draw of q (no counterpart in the
+ * paper). Use it where the random state of tnmc_mh_init can have
  * q = 0 in the arithmetic: in float32, the conditional of an unlikely forced
  * spin cancels to exactly 0 and such a chain would reject forever.
- * The forced first acceptance is counted in d_n_accept. */
+ * The forced first acceptance is counted in d_n_accept.
+ * Errors: TNMC_ERR_ARG (a NULL pointer), TNMC_ERR_CUDA. */
 tnmc_status tnmc_mh_init_empty(tnmc_handle *h, uint8_t *d_state_spins, double *d_state_logq,
                                double *d_state_E);
 
@@ -227,7 +238,8 @@ tnmc_status tnmc_mh_step(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop
                          double *d_state_logq, double *d_state_E, uint8_t *d_accept,
                          int64_t *d_n_accept);
 
-/* Optional diagnostic outputs, written by later calls until reset with NULL.
+/* Optional diagnostic outputs (the paper has no counterpart), written by later calls until
+ * reset with NULL. Errors: TNMC_ERR_ARG (NULL handle), TNMC_ERR_UNSUPPORTED (see Potts below).
  * d_logits : float32 [n_real * S * L^2] of propose / score: the logit of Eq. 5
  *            each draw was taken from (requires equal L for all realizations
  *            or is indexed like d_spins);
@@ -282,14 +294,17 @@ tnmc_status tnmc_set_diagnostics(tnmc_handle *h, float *d_logits, double *d_spec
 #define TNMC_MLP_PARAMS 5320
 #define TNMC_MLP_FEAT_STRIDE 8  /* floats per example row: x0 .. x6, then 0 */
 
-/* Use (enabled != 0) or stop using (enabled == 0, d_params_bf16 ignored) the
- * correction in later tnmc_propose, tnmc_propose_static, tnmc_score,
+/* Learned correction (no counterpart in the paper; its output enters q, Eq. 9, so
+ * Eq. 10 stays exact). Use (enabled != 0) or stop using (enabled == 0, d_params_bf16
+ * ignored) the correction in later tnmc_propose, tnmc_propose_static, tnmc_score,
  * tnmc_mh_init calls of this handle. d_params_bf16: device, 16-byte aligned,
  * TNMC_MLP_PARAMS bfloat16 values; the caller keeps it alive and unchanged
- * while those calls' kernels run. Errors: TNMC_ERR_ARG. */
+ * while those calls' kernels run. Errors: TNMC_ERR_ARG, TNMC_ERR_UNSUPPORTED (enabling it
+ * on a Potts handle). */
 tnmc_status tnmc_set_correction(tnmc_handle *h, const void *d_params_bf16, int32_t enabled);
 
-/* Training examples from S configurations per realization of this handle:
+/* Learned correction (no counterpart in the paper). Training examples from S
+ * configurations per realization of this handle:
  * the features of every site. d_spins: as in tnmc_score; d_logits: float32,
  * the uncorrected logits of those configurations (tnmc_score with the
  * diagnostic logits set and no correction); d_feat: float32
@@ -298,10 +313,12 @@ tnmc_status tnmc_set_correction(tnmc_handle *h, const void *d_params_bf16, int32
 tnmc_status tnmc_mlp_features(tnmc_handle *h, int32_t S, const uint8_t *d_spins,
                               const float *d_logits, float *d_feat);
 
-/* Floats of scratch tnmc_mlp_grad needs. */
+/* Floats of scratch tnmc_mlp_grad needs (the learned correction: no counterpart in the
+ * paper). Cannot fail. */
 size_t tnmc_mlp_scratch_floats(void);
 
-/* Mean binary cross entropy of sigmoid(x0 + Delta) against the target
+/* Learned correction (no counterpart in the paper). Mean binary cross entropy of
+ * sigmoid(x0 + Delta) against the target
  * probability sigmoid(t) and its gradient in the parameters (backpropagation,
  * the two bfloat16 roundings passed straight through), over a minibatch.
  * d_feat: float32 [n_ex][8]; d_target_logit: float32 [n_ex];
@@ -316,7 +333,8 @@ tnmc_status tnmc_mlp_grad(const float *d_feat, const float *d_target_logit, int6
                           int32_t B, uint64_t seed, int32_t step, const void *d_params_bf16,
                           float *d_grad, double *d_loss, float *d_scratch, void *stream);
 
-/* One Adam step (Kingma & Ba, 2015, bias-corrected; step counts from 1) on the
+/* Learned correction (no counterpart in the paper). One Adam step (Kingma & Ba, 2015,
+ * bias-corrected; step counts from 1) on the
  * float32 master copy d_master with moments d_m, d_v (all [TNMC_MLP_PARAMS],
  * updated in place), then the bfloat16 copy d_params_bf16 (round to nearest
  * even). Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
@@ -324,10 +342,12 @@ tnmc_status tnmc_mlp_adam(float *d_master, float *d_m, float *d_v, const float *
                           int32_t step, float lr, float beta1, float beta2, float eps,
                           void *d_params_bf16, void *stream);
 
-/* bfloat16 copy (round to nearest even) of a float32 parameter vector. */
+/* bfloat16 copy (round to nearest even) of a float32 parameter vector (the learned
+ * correction: no counterpart in the paper). Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
 tnmc_status tnmc_mlp_pack(const float *d_master, void *d_params_bf16, void *stream);
 
-/* Delta of n_ex example rows (d_feat as above) by the tensor-core network of
+/* Learned correction (no counterpart in the paper). Delta of n_ex example rows (d_feat
+ * as above) by the tensor-core network of
  * the sampler; d_delta: float32 [n_ex]. Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
 tnmc_status tnmc_mlp_forward(const float *d_feat, int64_t n_ex, const void *d_params_bf16,
                              float *d_delta, void *stream);
@@ -357,7 +377,8 @@ tnmc_status tnmc_mlp_forward(const float *d_feat, int64_t n_ex, const void *d_pa
 tnmc_status tnmc_propose_static(tnmc_handle *h, int32_t S, uint64_t seed, uint64_t prop_base,
                                 uint8_t *d_spins, double *d_logq, double *d_E);
 
-/* Bytes of the fixed device array used by tnmc_propose_static. */
+/* Bytes of the fixed device array used by tnmc_propose_static (no counterpart in the
+ * paper). Cannot fail. */
 size_t tnmc_propose_static_limit(void);
 
 /* Budget, in SM clock cycles, of every bounded device wait of this handle's
@@ -400,7 +421,7 @@ tnmc_status tnmc_set_realization_ids(tnmc_handle *h, const int64_t *h_ids);
  * handles). Errors: TNMC_ERR_ARG. */
 tnmc_status tnmc_set_build_variant(tnmc_handle *h, int32_t variant);
 
-/* The handle's current build layout (-1 for a NULL handle). */
+/* The handle's current build layout (-1 for a NULL handle; no counterpart in the paper). */
 int32_t tnmc_get_build_variant(const tnmc_handle *h);
 
 /* Autotuner of the build layout (the paper has no counterpart): ingests d_J (as
@@ -420,13 +441,16 @@ tnmc_status tnmc_autotune_build(tnmc_handle *h, const float *d_J, int32_t rows, 
                                 float *h_ms, int32_t *h_count);
 
 /* Copy the per-realization device flags (TNMC_FLAG_*) to h_flags [n_real],
- * after synchronising the stream; clears them when clear != 0.
+ * after synchronising the stream; clears them when clear != 0 (failure detection; the
+ * paper has no counterpart).
  * Returns TNMC_OK, or TNMC_ERR_NUMERIC / TNMC_ERR_TIMEOUT if any flag of
- * that kind is set (bad couplings map to TNMC_ERR_ARG). */
+ * that kind is set (bad couplings map to TNMC_ERR_ARG); TNMC_ERR_ARG for a NULL
+ * argument, TNMC_ERR_CUDA if the copy fails. */
 tnmc_status tnmc_get_device_status(tnmc_handle *h, int32_t *h_flags, int32_t clear);
 
-/* Sizes of the internal layout, for tests: bytes of the cache, of the
- * environment-build scratch and of the sampler scratch. */
+/* Sizes of the internal layout, for tests (no counterpart in the paper): bytes of the
+ * cache, of the environment-build scratch and of the sampler scratch; host only. A NULL
+ * output is skipped. Errors: as tnmc_workspace_size. */
 tnmc_status tnmc_layout_info(const tnmc_config *cfg, size_t *cache_bytes,
                              size_t *env_scratch_bytes, size_t *sample_scratch_bytes);
 

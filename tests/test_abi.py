@@ -116,3 +116,21 @@ def test_checkpointing_fits_the_L1024_workload(P):
     # MIXED (float64 build, float32 cache) also keeps its checkpoint rows in float64
     ws_mixed = P.workspace_size(Ls, 32, 3.0, P.TNMC_MIXED, 128, ckpt_every=32)
     assert ws_mixed - P.workspace_size(Ls, 32, 3.0, P.TNMC_FP32, 128, ckpt_every=32) >= 64 * 32 * 1024 * 32 * 32 * 8
+
+
+def test_every_declaration_cites_its_passage_and_errors():
+    """Each call of include/tnmc.h is documented on its own: a passage of the paper (Sec.,
+    Eq. or Fig.) or the statement that the paper has no counterpart, and its error
+    behaviour (the errors it returns, that it cannot fail, or what it returns)."""
+    import re
+    src = open(os.path.join(ROOT, "include", "tnmc.h")).read()
+    names = []
+    for m in re.finditer(r"^\w[\w\s\*]*?\b(tnmc_\w+)\(", src, re.M):
+        before = src[:m.start()]
+        c0, c1 = before.rfind("/*"), before.rfind("*/")
+        assert c0 >= 0 and c1 > c0 and before[c1 + 2:].strip() == "", m.group(1)
+        comment = " ".join(before[c0:c1].split())       # one line: phrases may wrap
+        assert re.search(r"Sec\.|Eq\.|Fig\.|no counterpart|does not state", comment), m.group(1)
+        assert re.search(r"Errors?:|Cannot fail|Returns|-1 for a NULL", comment), m.group(1)
+        names.append(m.group(1))
+    assert len(names) >= 29
